@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""EHYB FP64 SpMV benchmark on GB300.
+
+One step = one y = A x through the C ABI (ehyb_spmv: gather of x into the plan numbering +
+the fused slab/ER kernel writing y in the original numbering) on the 3D Q1 hex elasticity
+matrix (70^3 nodes x 3 dof: n = 1,029,000, nnz = 80,990,208), x ~ U[-1, 1) seeded.
+
+Prints ONE JSON line (rank 0).  value = whole-job GFLOP/s (2 nnz per SpMV, padding excluded)
+timed with CUDA events on the launching stream; the matrix (0.85 GB of slab) is larger than
+L2, so every step streams it from HBM.  Also reported:
+  * roofline of the fused kernel: its own CUDA-event time per launch, recorded by the library
+    around every launch in the timed region; algorithmic bytes from the plan (values + 16-bit
+    columns + ER columns + yIdxER/offsets + x + y) and algorithmic FLOPs (2 nnz);
+  * the plain vector-CSR kernel on the same GPU (original and EHYB-reordered row order, best
+    lanes-per-row of 1..32);
+  * preprocessing (plan build) time as a multiple of one SpMV;
+  * e2e: the same metric through ehyb_spmv_host with pinned host x / y copied every step;
+  * cpu_baseline: the CPU oracle (plain C CSR SpMV, one thread) on a bounded row sample.
+
+--impl reference times that oracle as the reference arm (there is no runnable reference code).
+Multi-GPU (torchrun): independent replicas, one per rank ("replicas only": the method's kernel
+has no exchange step at one GPU per rank), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EHYB SpMV GFLOP/s & % of HBM roofline vs plain CSR kernel on same GB300"
+HBM_FALLBACK_GBS = 6800.0
+# FP64 FMA pipe: 2 DFMA/clk/SM (1.25 TFLOP/s nominal for the part) x 2 flops x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "hex_elast3d_70": dict(kind="hex", N=70, seed_x=13,
+                           desc="3D Q1 hex elasticity, 70^3 nodes x 3 dof, jitter 0.2h, node relabelling"),
+    "fem2d_p1_200": dict(kind="fem2d", N=200, seed_x=3, desc="2D P1 Laplacian, 200^2 nodes, jitter 0.3h"),
+    "tet_lap3d_126": dict(kind="tet", N=126, seed_x=23, desc="3D P1 tet Laplacian, 126^3 nodes, Dirichlet"),
+}
+
+
+def make_matrix(w):
+    import gen
+    if w["kind"] == "hex":
+        return gen.hex_elast3d(N=w["N"])
+    if w["kind"] == "fem2d":
+        return gen.fem2d_p1(N=w["N"])
+    return gen.tet_lap3d(N=w["N"])
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 100 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            time.sleep(0.15)
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and "Active" in r[5 + i] and "Not" not in r[5 + i]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if len(r) > 3 and r[3].strip()[:1].isdigit())
+                if rows else None}
+
+
+def cpu_baseline(A, x, budget_s: float = 10.0):
+    """The oracle CSR SpMV (plain C, one thread) on a bounded sample: whole row blocks until budget."""
+    import oracle
+    n = A.n
+    y = np.zeros(n)
+    block = max(1, n // 16)
+    t0 = time.perf_counter()
+    rows = flops = 0
+    r = 0
+    while time.perf_counter() - t0 < budget_s:
+        r1 = min(n, r + block)
+        oracle.spmv_rows(A, x, r, r1, y)
+        flops += 2 * int(A.row_ptr[r1] - A.row_ptr[r])
+        rows += r1 - r
+        r = 0 if r1 >= n else r1
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows} rows in blocks of {block} of the same matrix (plain C CSR, 1 thread, {dt:.1f} s)"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    w = WORKLOADS[args.workload]
+    A = make_matrix(w)
+    import gen
+    x = gen.uniform(A.n, w["seed_x"])
+    y = np.zeros(A.n)
+    oracle.build()
+    # each step: one contiguous row block of the matrix, sized so the whole run takes ~60 s
+    steps = args.steps + args.warmup
+    t0 = time.perf_counter()
+    oracle.spmv_rows(A, x, 0, min(A.n, 4096), y)
+    per_row = (time.perf_counter() - t0) / min(A.n, 4096)
+    rows_per_step = int(max(64, min(A.n, 60.0 / max(steps, 1) / max(per_row, 1e-9))))
+    r = 0
+    flops = 0
+    t_total = 0.0
+    for i in range(steps):
+        r1 = min(A.n, r + rows_per_step)
+        t = time.perf_counter()
+        oracle.spmv_rows(A, x, r, r1, y)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            t_total += dt
+            flops += 2 * int(A.row_ptr[r1] - A.row_ptr[r])
+        r = 0 if r1 >= A.n else r1
+    value = flops / t_total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / max(args.steps, 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "desc": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"row blocks of {rows_per_step} rows per step (plain C CSR, 1 thread)"},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ehyb(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import gen
+    import paper_2204_06666_gb300 as eh
+
+    w = WORKLOADS[args.workload]
+    A = make_matrix(w)
+    x = gen.uniform(A.n, w["seed_x"])
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = eh.Plan(A)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    info = plan.info()
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.empty_like(xd)
+    flops_per_step = 2.0 * A.nnz
+
+    for _ in range(args.warmup):
+        plan.spmv(xd, yd)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        plan.profile_enable(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.spmv(xd, yd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = plan.profile_read()
+    plan.profile_enable(False)
+    clocks = clk.summary()
+    ms_max = ms
+    if pg:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = flops_per_step * args.steps * world / (ms_max / 1e3) / 1e9
+    ms_per_step = ms_max / args.steps
+
+    # ---- roofline of the fused kernel (its own per-launch event times from the timed region)
+    hbm_peak, peak_src = measured_peaks()
+    kern_s = kern_ms / 1e3 / max(kern_n, 1)
+    bytes_alg = float(info["bytes_effective"])
+    gbs = bytes_alg / kern_s / 1e9
+    fp64_tf = flops_per_step / kern_s / 1e12
+    fp64_peak = FP64_PEAK_TFLOPS
+    t_hbm = bytes_alg / (hbm_peak * 1e9)
+    t_alu = flops_per_step / (fp64_peak * 1e12)
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": fp64_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak,
+                "traffic": None, "peak_source": "nominal FP64 rate (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "peak_source": f"{peak_src} copy bandwidth"}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "peak_source": f"{peak_src} copy bandwidth",
+                "alu": {"achieved": fp64_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak}}
+    roof["kernel"] = "ehyb_kernel<double,double,scatter>"
+    roof["kernel_ms"] = kern_s * 1e3
+    roof["bytes_per_launch"] = bytes_alg
+    roof["nominal_8tbs_frac"] = gbs / 8000.0
+
+    # ---- plain CSR kernel on the same GPU (original order and EHYB order), best tpr
+    csr = {}
+    if not args.skip_csr:
+        n2o = plan.export()["new_to_old"]
+        o2n = np.empty(A.n, np.int64)
+        o2n[n2o] = np.arange(A.n)
+        for label, M in (("original_order", A), ("ehyb_order", _reorder(A, n2o, o2n))):
+            base = eh.CsrBaseline(M)
+            xx = xd if label == "original_order" else torch.from_numpy(x[n2o]).to(dev)
+            best = None
+            for tpr in (1, 2, 4, 8, 16, 32):
+                base.set_tpr(tpr)
+                for _ in range(3):
+                    base.spmv(xx, yd)
+                torch.cuda.synchronize()
+                reps = max(20, min(args.steps, 200))
+                e0.record(stream)
+                for _ in range(reps):
+                    base.spmv(xx, yd)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / reps
+                if best is None or t < best[1]:
+                    best = (tpr, t)
+            csr_bytes = A.nnz * 12 + (A.n + 1) * 8 + 16 * A.n
+            csr[label] = {"tpr": best[0], "ms": best[1], "gflops": flops_per_step / best[1] / 1e6,
+                          "gbs": csr_bytes / best[1] / 1e6}
+            base.close()
+        csr["ehyb_speedup_vs_best_csr"] = min(c["ms"] for c in csr.values() if isinstance(c, dict)) / ms_per_step
+
+    # ---- e2e through the public host entry (pinned host x, y copied every step)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        plan.spmv_host(xh, yh)
+    e2e_steps = max(10, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.spmv_host(xh, yh)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": flops_per_step * e2e_steps * world / e2e_s / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes),
+           "steps": e2e_steps, "api": "ehyb_spmv_host"}
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "desc": w["desc"],
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (0.85 GB slab streamed from HBM every step; x, y 16 MB)",
+                       "nparts": info["nparts"], "slice_rows": info["slice_rows"],
+                       "er_fraction": info["er_nnz"] / A.nnz, "er_tpr": info["er_tpr"],
+                       "block_threads": info["block_threads"]},
+            "effective_gbs": bytes_alg * args.steps * world / (ms_max / 1e3) / 1e9,
+            "roofline": roof, "csr_baseline": csr,
+            "preprocessing": {"plan_ms": plan_ms, "partition_ms": info["partition_ms"],
+                              "reorder_ms": info["reorder_ms"], "upload_ms": info["upload_ms"],
+                              "x_spmv": plan_ms / ms_per_step},
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, x, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def _reorder(A, n2o, o2n):
+    """P A P^T in CSR, rows in the plan numbering (columns relabelled, order kept)."""
+    import gen
+    lens = np.diff(A.row_ptr)[n2o]
+    rp = np.zeros(A.n + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    idx = _gather_rows(A.row_ptr, n2o, rp)
+    return gen.CSR(A.n, rp, o2n[A.col[idx]].astype(np.int32), A.val[idx], A.name + "_ehyb_order")
+
+
+def _gather_rows(row_ptr, n2o, rp_new):
+    starts = row_ptr[n2o]
+    lens = np.diff(rp_new)
+    out = np.repeat(starts - rp_new[:-1], lens) + np.arange(rp_new[-1])
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ehyb", choices=["ehyb", "reference"])
+    ap.add_argument("--workload", default="hex_elast3d_70", choices=sorted(WORKLOADS))
+    ap.add_argument("--skip-csr", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ehyb(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

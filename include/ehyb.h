@@ -1,0 +1,194 @@
+/*
+ * ehyb.h -- C ABI of the GB300 EHYB ("explicit caching hybrid") sparse matrix-vector
+ * library: y = A x with A sparse and square, x and y dense (Sec. 1).
+ *
+ * Method (Sec. 3, Sec. 4):
+ *   1. The rows of A are partitioned as an undirected graph so that most entries have
+ *      row and column in the same partition (Sec. 3.1; graph growing here, METIS in the
+ *      paper), with at most VecSize rows per partition chosen by Eq. 1 / Eq. 2 (Sec. 3.3).
+ *   2. Rows are renumbered partition by partition, each partition sorted by its number
+ *      of in-partition entries, descending (Alg. 1).
+ *   3. In-partition entries go to a sliced ELL slab (32-lane slices stored column-major)
+ *      with 16-bit column offsets into the partition's slice of x (Sec. 3.2, Sec. 3.4,
+ *      Alg. 2); the others go to the extra-rows (ER) part, each ER line mapped back to
+ *      its row by yIdxER (Sec. 3.2).
+ *   4. On the GPU one thread block per partition stages its slice of x into shared memory
+ *      with a bulk asynchronous copy, runs the slab from shared memory, then adds the ER
+ *      lines of its rows with global gathers (Alg. 3).
+ *
+ * Conventions for every call:
+ *   - Every function returns an ehyb_status_t and never aborts the process.
+ *   - Host pointers are only read during the call (borrowed); device pointers named
+ *     *_dev / x / y below are caller-owned device memory (cudaMalloc or torch), 8-byte
+ *     aligned for doubles; 16-byte alignment lets the staging use bulk copies.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - SpMV-type calls are asynchronous on `stream`; plan creation, ehyb_cg, ehyb_plan_info,
+ *     ehyb_plan_check and ehyb_plan_export synchronise.
+ *   - A plan owns device workspace: calls that use the same plan must not overlap in time
+ *     (issue them on one stream).  x and y must not alias.
+ *   - Device-detected faults (a staging wait that ran out of time) are recorded in a
+ *     per-plan status word and returned by the next ehyb_plan_check / ehyb_plan_info.
+ *   - Accepted matrices: square, 0 <= n < 2^31 - 1, nnz < 2^63; unsorted columns,
+ *     duplicate entries (summed like separate terms) and explicit zeros are kept; empty
+ *     rows give y_i = 0; n = 0 is a valid no-op.
+ *   - Non-finite entries of x: padding entries of the slab hold value 0 and column 0 of
+ *     their partition, so an Inf/NaN at that position of x can reach other rows of the
+ *     same slice as NaN.
+ */
+#ifndef EHYB_H
+#define EHYB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EHYB_OK = 0,
+  EHYB_ERR_INVALID_ARG = 1,   /* NULL where a pointer is required, bad option value */
+  EHYB_ERR_NOT_SQUARE = 2,    /* n_rows != n_cols */
+  EHYB_ERR_INDEX_RANGE = 3,   /* row_ptr not monotone / inconsistent, column out of [0, n) */
+  EHYB_ERR_TOO_LARGE = 4,     /* n >= 2^31 - 1, or a partition does not fit the shared-memory slice */
+  EHYB_ERR_OOM = 5,           /* host or device allocation failed */
+  EHYB_ERR_CUDA = 6,          /* a CUDA runtime call failed (see ehyb_last_cuda_error) */
+  EHYB_ERR_UNSUPPORTED = 7,   /* operation not available for this plan (e.g. host-only plan) */
+  EHYB_ERR_NOT_CONVERGED = 8, /* iterative solver stopped at max_iter */
+  EHYB_ERR_TIMEOUT = 9,       /* a bounded device-side wait ran out; results of that call are invalid */
+  EHYB_ERR_NO_DEVICE = 10     /* no CUDA device */
+} ehyb_status_t;
+
+typedef enum { EHYB_F64 = 0, EHYB_F32 = 1, EHYB_BF16 = 2 } ehyb_dtype_t;
+
+typedef struct {
+  int32_t slice_rows;        /* VecSize: max rows per partition; 0 = Eq. 1 / Eq. 2 default */
+  int32_t ell_width_cap;     /* max in-partition entries per row kept in the slab (rest -> ER); 0 = no cap */
+  int32_t ell_tpr;           /* lanes per row inside a 32-lane slab slice: 1,2,4,8,16,32; 0 = 1 */
+  int32_t er_tpr;            /* lanes per ER line (shuffle-reduced): 1,2,4,8,16,32; 0 = auto */
+  int32_t block_threads;     /* threads per block (multiple of 32, <= 1024); 0 = 512 */
+  int32_t lowp;              /* also store values as EHYB_F32 (1) or EHYB_BF16 (2) for the FP32 kernels; 0 = no */
+  int32_t host_only;         /* 1: build the format on the host only (inspection, no GPU use) */
+  int32_t num_sms;           /* P of Eq. 1 for host-only plans; 0 = query the current device */
+  int32_t smem_budget;       /* SHM^max of Eq. 1 in bytes per block; 0 = device opt-in maximum - 1024 */
+  const int32_t* part_vec;   /* optional PartVec (one partition id >= 0 per row); NULL = in-house partitioner */
+  int64_t wait_timeout_ns;   /* bound on each device-side wait; 0 = 1e9 (one second) */
+  int32_t inject_wait_fault; /* test hook: the staging wait waits for a copy that is never issued */
+  int32_t keep_host;         /* keep host copies of the plan arrays (ehyb_plan_export without device reads) */
+  uint64_t seed;             /* reserved for randomised partitioners; the in-house one is deterministic */
+} ehyb_options_t;
+
+typedef struct ehyb_plan_s* ehyb_plan_t;
+typedef struct ehyb_csr_s* ehyb_csr_t;
+
+typedef struct {
+  int64_t n, nnz;
+  int32_t nparts, nslices, slice_rows, ell_tpr, er_tpr, block_threads, smem_bytes, lowp;
+  int64_t ell_nnz;           /* entries in the slab (without padding) */
+  int64_t ell_stored;        /* slab slots including padding */
+  int64_t er_rows, er_nnz;   /* ER lines and their entries */
+  int64_t bytes_effective;   /* algorithmic bytes of one FP64 SpMV (see ehyb_spmv) */
+  int64_t bytes_device;      /* device memory held by the plan */
+  double partition_ms, reorder_ms, upload_ms;
+  int32_t device_status;     /* EHYB_OK or the first fault recorded by a kernel */
+  int32_t num_sms;
+} ehyb_plan_info_t;
+
+/* Pointers into arrays owned by the plan (valid until ehyb_destroy); see ehyb_plan_export. */
+typedef struct {
+  int64_t n;
+  int32_t nparts, nslices, tpr;
+  int64_t ell_stored, er_rows, er_nnz;
+  const int32_t* new_to_old;     /* [n]: original index of new row i (inverse of ReorderTable) */
+  const int32_t* part_ptr;       /* [nparts+1]: partBoundary, partition p = new rows [part_ptr[p], part_ptr[p+1]) */
+  const int32_t* slice_ptr;      /* [nparts+1]: slices of partition p */
+  const int64_t* slice_pos;      /* [nslices+1]: PositionELL; slice width = (slice_pos[s+1]-slice_pos[s])/32 */
+  const uint16_t* ell_col;       /* [ell_stored]: ColELL, column - part_ptr[p] (16-bit offset into the slice) */
+  const double* ell_val;         /* [ell_stored]: ValELL; slot of (lane, k) = slice_pos[s] + 32 k + lane */
+  const int32_t* row_ell_count;  /* [n]: slab entries of each new row (slots k*tpr+sub < count are real) */
+  const int32_t* er_part_ptr;    /* [nparts+1]: ER lines owned by partition p */
+  const int32_t* er_row;         /* [er_rows]: yIdxER, the new row of each ER line */
+  const int64_t* er_ptr;         /* [er_rows+1]: CSR offsets of the ER lines */
+  const int32_t* er_col;         /* [er_nnz]: new-numbering column */
+  const double* er_val;          /* [er_nnz] */
+} ehyb_plan_export_t;
+
+const char* ehyb_status_string(ehyb_status_t s);
+/* Text of the last CUDA error seen by this library in this thread ("" if none). */
+const char* ehyb_last_cuda_error(void);
+void ehyb_options_default(ehyb_options_t* opt);
+
+/*
+ * Build a plan from a host CSR matrix (Alg. 1 and Alg. 2, Sec. 4.1) and upload it.
+ * row_ptr: int64[n_rows+1], col: int32[nnz], val: double[nnz], all host memory.
+ * opt: NULL for defaults.  Synchronous.  On success *out owns host and device memory.
+ */
+ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col, const double* val, const ehyb_options_t* opt,
+                                   void* stream, ehyb_plan_t* out);
+
+/* Release a plan (NULL is accepted).  Synchronises the device before freeing. */
+ehyb_status_t ehyb_destroy(ehyb_plan_t plan);
+
+/*
+ * y = A x in FP64 (Alg. 3), x and y device arrays of n doubles in the ORIGINAL numbering.
+ * Launches: a gather x_p = x[new_to_old] into plan workspace, then one block per partition
+ * (stage slice of x_p into shared memory, slab from shared memory, ER lines with global
+ * gathers) writing y[new_to_old[r]] directly.  Effective bytes per call (ehyb_plan_info):
+ * 10 per slab entry (value + 16-bit column), 12 per ER entry, 8 per ER line (yIdxER and its
+ * CSR offset), and 8 n each for x and y.
+ */
+ehyb_status_t ehyb_spmv(ehyb_plan_t plan, const double* x, double* y, void* stream);
+
+/* y_p = A_p x_p in the plan's numbering (x_p[i] = x[new_to_old[i]]): one kernel, no gathers. */
+ehyb_status_t ehyb_spmv_permuted(ehyb_plan_t plan, const double* xp, double* yp, void* stream);
+
+/* out = in reordered: to_new != 0 gives out[i] = in[new_to_old[i]], else out[new_to_old[i]] = in[i]. */
+ehyb_status_t ehyb_permute(ehyb_plan_t plan, int32_t to_new, const double* in, double* out, void* stream);
+
+/*
+ * y = A x with HOST x and y (n doubles each): copies x in, runs ehyb_spmv, copies y out, on
+ * `stream`, and waits for the stream.  Pinned host memory makes the copies asynchronous DMA.
+ */
+ehyb_status_t ehyb_spmv_host(ehyb_plan_t plan, const double* x_host, double* y_host, void* stream);
+
+/* y = A_low x in FP32 arithmetic with values stored as opt.lowp (FP32 or BF16), x and y float
+ * device arrays in the original numbering.  EHYB_ERR_UNSUPPORTED if the plan has no lowp copy. */
+ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t plan, const float* x, float* y, void* stream);
+
+/* Plan statistics; synchronises and reads the device status word. */
+ehyb_status_t ehyb_plan_info(ehyb_plan_t plan, ehyb_plan_info_t* info);
+
+/* Synchronise the device and return the plan's device status word (then clear it). */
+ehyb_status_t ehyb_plan_check(ehyb_plan_t plan);
+
+/* Fill *ex with pointers to host copies of the plan arrays (copied back from the device
+ * on first use when the plan did not keep them).  Valid until ehyb_destroy. */
+ehyb_status_t ehyb_plan_export(ehyb_plan_t plan, ehyb_plan_export_t* ex);
+
+/*
+ * Kernel timing: while enabled, every SpMV call on the plan records a CUDA event pair around
+ * its main (slab + ER) kernel on the launch stream; ehyb_profile_read synchronises and returns
+ * the summed milliseconds and the number of timed launches since the last enable.
+ */
+ehyb_status_t ehyb_profile_enable(ehyb_plan_t plan, int32_t enable);
+ehyb_status_t ehyb_profile_read(ehyb_plan_t plan, double* total_ms, int64_t* launches);
+
+/* ---- plain CSR baseline (vector CSR: tpr lanes per row, shuffle reduction; Sec. 2.2) ---- */
+
+/* Upload a CSR matrix (host arrays as for ehyb_plan_create_csr).  tpr: 1..32 power of two, 0 = auto. */
+ehyb_status_t ehyb_csr_create(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const double* val,
+                              int32_t tpr, void* stream, ehyb_csr_t* out);
+ehyb_status_t ehyb_csr_spmv(ehyb_csr_t m, const double* x, double* y, void* stream);
+ehyb_status_t ehyb_csr_set_tpr(ehyb_csr_t m, int32_t tpr);
+ehyb_status_t ehyb_csr_destroy(ehyb_csr_t m);
+
+/* ---- test hook (host-side fault injection) ---- */
+
+/* Allow `count` more device allocations by this library, then fail them with EHYB_ERR_OOM;
+ * a negative count switches the hook off.  Used to test the out-of-memory paths. */
+void ehyb_test_fail_allocs_after(int32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EHYB_H */

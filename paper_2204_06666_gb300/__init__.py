@@ -1,0 +1,311 @@
+"""Python binding of libehyb.so, the GB300 EHYB SpMV library (C ABI in include/ehyb.h).
+
+Argument marshalling only: every step of the SpMV runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams; numpy arrays carry host CSR data.  The
+module-level functions carry the C names (``ehyb_plan_create_csr``, ``ehyb_spmv`` ...);
+``Plan`` and ``CsrBaseline`` wrap them with exceptions and ownership.
+
+There is no fallback: if libehyb.so is missing the import fails with instructions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libehyb.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(or python paper_2204_06666_gb300/build.py) first")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+STATUS = {0: "EHYB_OK", 1: "EHYB_ERR_INVALID_ARG", 2: "EHYB_ERR_NOT_SQUARE", 3: "EHYB_ERR_INDEX_RANGE",
+          4: "EHYB_ERR_TOO_LARGE", 5: "EHYB_ERR_OOM", 6: "EHYB_ERR_CUDA", 7: "EHYB_ERR_UNSUPPORTED",
+          8: "EHYB_ERR_NOT_CONVERGED", 9: "EHYB_ERR_TIMEOUT", 10: "EHYB_ERR_NO_DEVICE"}
+EHYB_OK, EHYB_ERR_TIMEOUT, EHYB_ERR_NOT_CONVERGED = 0, 9, 8
+
+
+class EhybError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        msg = _lib.ehyb_status_string(self.status).decode()
+        cuda = _lib.ehyb_last_cuda_error().decode()
+        super().__init__(f"{where}: {STATUS.get(self.status, self.status)} ({msg})" + (f" [{cuda}]" if cuda else ""))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("slice_rows", ctypes.c_int32), ("ell_width_cap", ctypes.c_int32), ("ell_tpr", ctypes.c_int32),
+                ("er_tpr", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("lowp", ctypes.c_int32),
+                ("host_only", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("smem_budget", ctypes.c_int32),
+                ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
+                ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nparts", ctypes.c_int32),
+                ("nslices", ctypes.c_int32), ("slice_rows", ctypes.c_int32), ("ell_tpr", ctypes.c_int32),
+                ("er_tpr", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("lowp", ctypes.c_int32), ("ell_nnz", ctypes.c_int64), ("ell_stored", ctypes.c_int64),
+                ("er_rows", ctypes.c_int64), ("er_nnz", ctypes.c_int64), ("bytes_effective", ctypes.c_int64),
+                ("bytes_device", ctypes.c_int64), ("partition_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
+                ("upload_ms", ctypes.c_double), ("device_status", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PlanExport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nparts", ctypes.c_int32), ("nslices", ctypes.c_int32),
+                ("tpr", ctypes.c_int32), ("ell_stored", ctypes.c_int64), ("er_rows", ctypes.c_int64),
+                ("er_nnz", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in (
+                    "new_to_old", "part_ptr", "slice_ptr", "slice_pos", "ell_col", "ell_val", "row_ell_count",
+                    "er_part_ptr", "er_row", "er_ptr", "er_col", "er_val")]
+
+
+_P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("ehyb_status_string", [ctypes.c_int], ctypes.c_char_p)
+_sig("ehyb_last_cuda_error", [], ctypes.c_char_p)
+_sig("ehyb_options_default", [ctypes.POINTER(Options)], None)
+_sig("ehyb_test_fail_allocs_after", [_I32], None)
+_sig("ehyb_plan_create_csr", [_I64, _I64, _I64, _P, _P, _P, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)])
+_sig("ehyb_destroy", [_P])
+_sig("ehyb_spmv", [_P, _P, _P, _P])
+_sig("ehyb_spmv_permuted", [_P, _P, _P, _P])
+_sig("ehyb_permute", [_P, _I32, _P, _P, _P])
+_sig("ehyb_spmv_host", [_P, _P, _P, _P])
+_sig("ehyb_spmv_lowp", [_P, _P, _P, _P])
+_sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
+_sig("ehyb_plan_check", [_P])
+_sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
+_sig("ehyb_profile_enable", [_P, _I32])
+_sig("ehyb_profile_read", [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)])
+_sig("ehyb_csr_create", [_I64, _I64, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)])
+_sig("ehyb_csr_spmv", [_P, _P, _P, _P])
+_sig("ehyb_csr_set_tpr", [_P, _I32])
+_sig("ehyb_csr_destroy", [_P])
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise EhybError(st, where)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t, dtype_name: str) -> int:
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch." + dtype_name):
+        raise TypeError(f"expected a contiguous CUDA torch.{dtype_name} tensor, got {t.dtype} on {t.device}")
+    return t.data_ptr()
+
+
+def _host(a, dtype) -> int:
+    if hasattr(a, "data_ptr") and not hasattr(a, "ctypes"):  # torch CPU tensor (possibly pinned)
+        if a.is_cuda or not a.is_contiguous():
+            raise TypeError("expected a contiguous CPU tensor")
+        return a.data_ptr()
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a contiguous numpy {np.dtype(dtype)} array")
+    return a.ctypes.data
+
+
+def make_options(**kw) -> Options:
+    o = Options()
+    _lib.ehyb_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "part_vec":
+            continue
+        setattr(o, k, int(v))
+    return o
+
+
+# ---------------------------------------------------------------- C-named thin wrappers
+
+def ehyb_plan_create_csr(n_rows, n_cols, nnz, row_ptr, col, val, opt: Options | None, stream, out: ctypes.c_void_p):
+    return _lib.ehyb_plan_create_csr(n_rows, n_cols, nnz, row_ptr, col, val,
+                                     ctypes.byref(opt) if opt is not None else None, stream, ctypes.byref(out))
+
+
+def ehyb_destroy(plan):
+    return _lib.ehyb_destroy(plan)
+
+
+def ehyb_spmv(plan, x, y, stream):
+    return _lib.ehyb_spmv(plan, x, y, stream)
+
+
+def ehyb_spmv_permuted(plan, xp, yp, stream):
+    return _lib.ehyb_spmv_permuted(plan, xp, yp, stream)
+
+
+def ehyb_permute(plan, to_new, x, y, stream):
+    return _lib.ehyb_permute(plan, to_new, x, y, stream)
+
+
+def ehyb_spmv_host(plan, x, y, stream):
+    return _lib.ehyb_spmv_host(plan, x, y, stream)
+
+
+def ehyb_spmv_lowp(plan, x, y, stream):
+    return _lib.ehyb_spmv_lowp(plan, x, y, stream)
+
+
+def ehyb_plan_check(plan):
+    return _lib.ehyb_plan_check(plan)
+
+
+def ehyb_test_fail_allocs_after(count: int):
+    _lib.ehyb_test_fail_allocs_after(count)
+
+
+# ---------------------------------------------------------------- owning wrappers
+
+class Plan:
+    """An EHYB plan built from a host CSR matrix (anything with n, row_ptr, col, val)."""
+
+    def __init__(self, A, stream=None, part_vec=None, **opts):
+        self._h = ctypes.c_void_p()
+        rp = np.ascontiguousarray(A.row_ptr, np.int64)
+        c = np.ascontiguousarray(A.col, np.int32)
+        v = np.ascontiguousarray(A.val, np.float64)
+        n = int(A.n)
+        n_cols = int(opts.pop("n_cols", n))
+        o = make_options(**opts)
+        pv = None
+        if part_vec is not None:
+            pv = np.ascontiguousarray(part_vec, np.int32)
+            o.part_vec = pv.ctypes.data
+        self.host_only = bool(opts.get("host_only", 0))
+        s = None if self.host_only else _stream(stream)
+        st = ehyb_plan_create_csr(n, n_cols, int(rp[-1]) if rp.size else 0, rp.ctypes.data, c.ctypes.data,
+                                  v.ctypes.data, o, s, self._h)
+        _check(st, "ehyb_plan_create_csr")
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _check(_lib.ehyb_destroy(self._h), "ehyb_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.ehyb_destroy(self._h)
+        except Exception:
+            pass
+
+    def spmv(self, x, y, stream=None):
+        _check(ehyb_spmv(self._h, _dev(x, "float64"), _dev(y, "float64"), _stream(stream)), "ehyb_spmv")
+
+    def spmv_permuted(self, xp, yp, stream=None):
+        _check(ehyb_spmv_permuted(self._h, _dev(xp, "float64"), _dev(yp, "float64"), _stream(stream)),
+               "ehyb_spmv_permuted")
+
+    def permute(self, to_new: bool, x, y, stream=None):
+        _check(ehyb_permute(self._h, int(bool(to_new)), _dev(x, "float64"), _dev(y, "float64"), _stream(stream)),
+               "ehyb_permute")
+
+    def spmv_host(self, x, y, stream=None):
+        _check(ehyb_spmv_host(self._h, _host(x, np.float64), _host(y, np.float64), _stream(stream)),
+               "ehyb_spmv_host")
+
+    def spmv_lowp(self, x, y, stream=None):
+        _check(ehyb_spmv_lowp(self._h, _dev(x, "float32"), _dev(y, "float32"), _stream(stream)), "ehyb_spmv_lowp")
+
+    def check(self) -> int:
+        return int(ehyb_plan_check(self._h))
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(_lib.ehyb_plan_info(self._h, ctypes.byref(inf)), "ehyb_plan_info")
+        return inf.as_dict()
+
+    def export(self) -> dict:
+        ex = PlanExport()
+        _check(_lib.ehyb_plan_export(self._h, ctypes.byref(ex)), "ehyb_plan_export")
+        n, nparts, ns = ex.n, ex.nparts, ex.nslices
+
+        def arr(ptr, count, dt):
+            if count == 0 or not ptr:
+                return np.zeros(count, dt)
+            return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt))),
+                                         (count,)).copy()
+
+        return {"n": n, "tpr": ex.tpr, "nparts": nparts,
+                "new_to_old": arr(ex.new_to_old, n, np.int32), "part_ptr": arr(ex.part_ptr, nparts + 1, np.int32),
+                "slice_ptr": arr(ex.slice_ptr, nparts + 1, np.int32),
+                "slice_pos": arr(ex.slice_pos, ns + 1, np.int64),
+                "ell_col": arr(ex.ell_col, ex.ell_stored, np.uint16),
+                "ell_val": arr(ex.ell_val, ex.ell_stored, np.float64),
+                "row_ell_count": arr(ex.row_ell_count, n, np.int32),
+                "er_part_ptr": arr(ex.er_part_ptr, nparts + 1, np.int32),
+                "er_row": arr(ex.er_row, ex.er_rows, np.int32), "er_ptr": arr(ex.er_ptr, ex.er_rows + 1, np.int64),
+                "er_col": arr(ex.er_col, ex.er_nnz, np.int32), "er_val": arr(ex.er_val, ex.er_nnz, np.float64)}
+
+    def profile_enable(self, on: bool = True):
+        _check(_lib.ehyb_profile_enable(self._h, int(on)), "ehyb_profile_enable")
+
+    def profile_read(self):
+        ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
+        _check(_lib.ehyb_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)), "ehyb_profile_read")
+        return ms.value, cnt.value
+
+
+class CsrBaseline:
+    """The plain vector-CSR kernel on the same GPU (tpr lanes per row)."""
+
+    def __init__(self, A, tpr: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        rp = np.ascontiguousarray(A.row_ptr, np.int64)
+        c = np.ascontiguousarray(A.col, np.int32)
+        v = np.ascontiguousarray(A.val, np.float64)
+        _check(_lib.ehyb_csr_create(int(A.n), int(rp[-1]), rp.ctypes.data, c.ctypes.data, v.ctypes.data, tpr,
+                                    _stream(stream), ctypes.byref(self._h)), "ehyb_csr_create")
+        self.n = int(A.n)
+
+    def set_tpr(self, tpr: int):
+        _check(_lib.ehyb_csr_set_tpr(self._h, tpr), "ehyb_csr_set_tpr")
+
+    def spmv(self, x, y, stream=None):
+        _check(_lib.ehyb_csr_spmv(self._h, _dev(x, "float64"), _dev(y, "float64"), _stream(stream)),
+               "ehyb_csr_spmv")
+
+    def close(self):
+        if self._h:
+            _check(_lib.ehyb_csr_destroy(self._h), "ehyb_csr_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.ehyb_csr_destroy(self._h)
+        except Exception:
+            pass

@@ -1,0 +1,622 @@
+// C ABI of the EHYB library (declared in include/ehyb.h): argument validation, option
+// resolution (Eq. 1 default for VecSize), host planning, upload, kernel launches, profiling.
+#include "../../include/ehyb.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "device.h"
+#include "plan.h"
+
+using namespace ehyb;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+int g_fail_allocs_after = -1;  // test hook: >= 0 makes that many successful device allocations, then fail
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+ehyb_status_t cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  g_cuda_err = buf;
+  return EHYB_ERR_CUDA;
+}
+
+#define CK(call)                                                      \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);               \
+  } while (0)
+
+ehyb_status_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return EHYB_OK;
+  if (g_fail_allocs_after == 0) return EHYB_ERR_OOM;
+  if (g_fail_allocs_after > 0) --g_fail_allocs_after;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return EHYB_ERR_OOM;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  return EHYB_OK;
+}
+
+bool is_pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+int pow2_near(double v) {  // power of two nearest to v in [1, 32]
+  int p = 1;
+  while (p < 32 && (double)p * 1.41421356 < v) p <<= 1;
+  return p;
+}
+
+struct DeviceInfo {
+  int dev = -1, sms = 0, smem_optin = 0;
+};
+
+ehyb_status_t query_device(DeviceInfo& d) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    return EHYB_ERR_NO_DEVICE;
+  }
+  CK(cudaGetDevice(&d.dev));
+  CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, d.dev));
+  CK(cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d.dev));
+  static int inited_dev[64] = {0};
+  if (d.dev >= 0 && d.dev < 64 && !inited_dev[d.dev]) {
+    CK(kernels_init(d.smem_optin - 1024));  // static shared memory and alignment slack stay outside
+    inited_dev[d.dev] = 1;
+  }
+  return EHYB_OK;
+}
+
+// 256-byte aligned sub-allocations of one device arena
+struct Arena {
+  size_t size = 0;
+  template <typename T>
+  size_t add(size_t count) {
+    size_t off = size;
+    size += ((count * sizeof(T)) + 255) & ~(size_t)255;
+    return off;
+  }
+};
+
+ehyb_status_t validate_csr(int64_t nr, int64_t nc, int64_t nnz, const int64_t* rp, const int32_t* col,
+                           const double* val) {
+  if (nr < 0 || nc < 0 || nnz < 0) return EHYB_ERR_INVALID_ARG;
+  if (nr != nc) return EHYB_ERR_NOT_SQUARE;
+  if (nr >= (int64_t)INT32_MAX - 1) return EHYB_ERR_TOO_LARGE;
+  if (!rp) return EHYB_ERR_INVALID_ARG;
+  if (nnz > 0 && (!col || !val)) return EHYB_ERR_INVALID_ARG;
+  if (rp[0] != 0 || rp[nr] != nnz) return EHYB_ERR_INDEX_RANGE;
+  for (int64_t i = 0; i < nr; ++i)
+    if (rp[i + 1] < rp[i]) return EHYB_ERR_INDEX_RANGE;
+  for (int64_t k = 0; k < nnz; ++k)
+    if (col[k] < 0 || (int64_t)col[k] >= nc) return EHYB_ERR_INDEX_RANGE;
+  return EHYB_OK;
+}
+
+}  // namespace
+
+struct ehyb_plan_s {
+  HostPlan host;        // arrays kept only when requested (or host-only); metadata always
+  bool host_kept = false;
+  bool host_only = false;
+  DevPlan dev;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  double* xp = nullptr;     // FP64 workspace (plan numbering), n + 2
+  float* xp32 = nullptr;    // FP32 workspace
+  double* hx = nullptr;     // device staging for ehyb_spmv_host
+  double* hy = nullptr;
+  int32_t lowp = 0;
+  int32_t er_tpr = 1;
+  int64_t ell_nnz = 0, ell_stored = 0, er_rows = 0, er_nnz = 0;
+  int32_t nslices = 0, slice_rows = 0, num_sms = 0;
+  double upload_ms = 0;
+  int device = -1;
+  // profiling
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  // export copies (host)
+  bool exported = false;
+};
+
+struct ehyb_csr_s {
+  int64_t n = 0, nnz = 0;
+  int32_t tpr = 1;
+  int64_t* rp = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+
+extern "C" {
+
+const char* ehyb_status_string(ehyb_status_t s) {
+  switch (s) {
+    case EHYB_OK: return "ok";
+    case EHYB_ERR_INVALID_ARG: return "invalid argument";
+    case EHYB_ERR_NOT_SQUARE: return "matrix is not square";
+    case EHYB_ERR_INDEX_RANGE: return "row pointer or column index out of range";
+    case EHYB_ERR_TOO_LARGE: return "matrix or partition too large";
+    case EHYB_ERR_OOM: return "out of memory";
+    case EHYB_ERR_CUDA: return "CUDA error";
+    case EHYB_ERR_UNSUPPORTED: return "unsupported for this plan";
+    case EHYB_ERR_NOT_CONVERGED: return "not converged";
+    case EHYB_ERR_TIMEOUT: return "device wait timed out";
+    case EHYB_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+const char* ehyb_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+void ehyb_options_default(ehyb_options_t* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+}
+
+// test hook (host-side fault injection): allow `count` more device allocations, then fail with
+// EHYB_ERR_OOM; a negative count disables the hook.
+void ehyb_test_fail_allocs_after(int32_t count) { g_fail_allocs_after = count; }
+
+ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col, const double* val, const ehyb_options_t* opt_in,
+                                   void* stream, ehyb_plan_t* out) {
+  if (!out) return EHYB_ERR_INVALID_ARG;
+  *out = nullptr;
+  ehyb_status_t st = validate_csr(n_rows, n_cols, nnz, row_ptr, col, val);
+  if (st != EHYB_OK) return st;
+  ehyb_options_t opt;
+  ehyb_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.ell_tpr == 0) opt.ell_tpr = 1;
+  if (!is_pow2_in(opt.ell_tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
+  if (opt.er_tpr != 0 && !is_pow2_in(opt.er_tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
+  if (opt.block_threads == 0) opt.block_threads = 512;
+  if (opt.block_threads < 32 || opt.block_threads > 1024 || opt.block_threads % 32) return EHYB_ERR_INVALID_ARG;
+  if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
+      opt.num_sms < 0 || opt.wait_timeout_ns < 0)
+    return EHYB_ERR_INVALID_ARG;
+  if (opt.slice_rows > 65536) return EHYB_ERR_TOO_LARGE;
+  const int64_t n = n_rows;
+  if (opt.part_vec)
+    for (int64_t i = 0; i < n; ++i)
+      if (opt.part_vec[i] < 0 || opt.part_vec[i] >= INT32_MAX - 1) return EHYB_ERR_INVALID_ARG;
+
+  DeviceInfo d;
+  if (!opt.host_only) {
+    st = query_device(d);
+    if (st != EHYB_OK) return st;
+  } else {
+    d.sms = opt.num_sms > 0 ? opt.num_sms : 152;
+    d.smem_optin = 232448;
+  }
+  const int64_t budget = opt.smem_budget > 0 ? opt.smem_budget : (int64_t)d.smem_optin - 1024;
+  if (opt.num_sms > 0) d.sms = opt.num_sms;
+
+  std::unique_ptr<ehyb_plan_s> P;
+  try {
+    P.reset(new ehyb_plan_s());
+  } catch (const std::bad_alloc&) {
+    return EHYB_ERR_OOM;
+  }
+  PlanParams prm;
+  prm.n = n;
+  // Eq. 1 / Eq. 2 with tau = 8 (FP64 x slice), keeping 32 bytes of rounding and alignment slack
+  prm.slice_rows = opt.slice_rows > 0 ? opt.slice_rows : eq1_slice_rows(n, 8, d.sms, budget - 32);
+  prm.ell_width_cap = opt.ell_width_cap;
+  prm.ell_tpr = opt.ell_tpr;
+  prm.lowp = opt.lowp;
+  prm.part_vec = opt.part_vec;
+  HostPlan& H = P->host;
+  try {
+    int rc = build_plan(prm, row_ptr, col, val, H);
+    if (rc != 0) return (ehyb_status_t)rc;
+  } catch (const std::bad_alloc&) {
+    return EHYB_ERR_OOM;
+  }
+  // every partition's slice of x (FP64, plus 16-byte alignment slack) must fit one block's dynamic shared memory
+  if ((int64_t)(H.max_part_rows + 2) * 8 > (int64_t)d.smem_optin - 1024) return EHYB_ERR_TOO_LARGE;
+
+  P->host_only = opt.host_only != 0;
+  P->lowp = opt.lowp;
+  P->num_sms = d.sms;
+  P->slice_rows = prm.slice_rows;
+  P->ell_nnz = H.ell_nnz;
+  P->ell_stored = (int64_t)H.ell_col.size();
+  P->er_rows = (int64_t)H.er_row.size();
+  P->er_nnz = (int64_t)H.er_col.size();
+  P->nslices = H.nslices;
+  if (opt.er_tpr) {
+    P->er_tpr = opt.er_tpr;
+  } else {
+    double mean = P->er_rows ? (double)P->er_nnz / (double)P->er_rows : 1.0;
+    P->er_tpr = pow2_near(mean / 6.0);
+  }
+  DevPlan& D = P->dev;
+  D.n = n;
+  D.nparts = H.nparts;
+  D.tpr = H.tpr;
+  D.er_tpr = P->er_tpr;
+  D.threads = opt.block_threads;
+  D.max_part_rows = H.max_part_rows;
+  D.wait_timeout_ns = opt.wait_timeout_ns > 0 ? (uint64_t)opt.wait_timeout_ns : 1000000000ull;
+  D.inject_wait_fault = opt.inject_wait_fault;
+
+  if (!P->host_only) {
+    const double t0 = now_ms();
+    P->device = d.dev;
+    cudaStream_t s = (cudaStream_t)stream;
+    Arena A;
+    const size_t o_n2o = A.add<int32_t>((size_t)n);
+    const size_t o_pp = A.add<int32_t>(H.part_ptr.size());
+    const size_t o_sp = A.add<int32_t>(H.slice_ptr.size());
+    const size_t o_pos = A.add<int64_t>(H.slice_pos.size());
+    const size_t o_ec = A.add<uint16_t>(H.ell_col.size());
+    const size_t o_ev = A.add<double>(H.ell_val.size());
+    const size_t o_ev32 = A.add<float>(H.ell_val_f32.size());
+    const size_t o_ev16 = A.add<uint16_t>(H.ell_val_bf16.size());
+    const size_t o_epp = A.add<int32_t>(H.er_part_ptr.size());
+    const size_t o_er = A.add<int32_t>(H.er_row.size());
+    const size_t o_erp = A.add<int64_t>(H.er_ptr.size());
+    const size_t o_erc = A.add<int32_t>(H.er_col.size());
+    const size_t o_erv = A.add<double>(H.er_val.size());
+    const size_t o_erv32 = A.add<float>(H.er_val_f32.size());
+    const size_t o_erv16 = A.add<uint16_t>(H.er_val_bf16.size());
+    const size_t o_xp = A.add<double>((size_t)n + 2);
+    const size_t o_xp32 = A.add<float>((size_t)n + 4);
+    const size_t o_st = A.add<int32_t>(4);
+    st = dev_alloc(&P->arena, A.size);
+    if (st != EHYB_OK) return st;
+    P->arena_bytes = A.size;
+    char* base = (char*)P->arena;
+    auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+      if (bytes == 0) return cudaSuccess;
+      return cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    cudaError_t e = cudaSuccess;
+#define UP(off, vec)                                                                  \
+  if (e == cudaSuccess) e = up(off, vec.data(), vec.size() * sizeof(vec[0]));
+    UP(o_n2o, H.new_to_old) UP(o_pp, H.part_ptr) UP(o_sp, H.slice_ptr) UP(o_pos, H.slice_pos) UP(o_ec, H.ell_col)
+    UP(o_ev, H.ell_val) UP(o_ev32, H.ell_val_f32) UP(o_ev16, H.ell_val_bf16) UP(o_epp, H.er_part_ptr)
+    UP(o_er, H.er_row) UP(o_erp, H.er_ptr) UP(o_erc, H.er_col) UP(o_erv, H.er_val) UP(o_erv32, H.er_val_f32)
+    UP(o_erv16, H.er_val_bf16)
+#undef UP
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_st, 0, 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_xp, 0, ((size_t)n + 2) * 8, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaFree(P->arena);
+      P->arena = nullptr;
+      return cuda_fail(e, "plan upload");
+    }
+    D.new_to_old = (const int32_t*)(base + o_n2o);
+    D.part_ptr = (const int32_t*)(base + o_pp);
+    D.slice_ptr = (const int32_t*)(base + o_sp);
+    D.slice_pos = (const int64_t*)(base + o_pos);
+    D.ell_col = (const uint16_t*)(base + o_ec);
+    D.ell_val = (const double*)(base + o_ev);
+    D.ell_val_f32 = (const float*)(base + o_ev32);
+    D.ell_val_bf16 = (const uint16_t*)(base + o_ev16);
+    D.er_part_ptr = (const int32_t*)(base + o_epp);
+    D.er_row = (const int32_t*)(base + o_er);
+    D.er_ptr = (const int64_t*)(base + o_erp);
+    D.er_col = (const int32_t*)(base + o_erc);
+    D.er_val = (const double*)(base + o_erv);
+    D.er_val_f32 = (const float*)(base + o_erv32);
+    D.er_val_bf16 = (const uint16_t*)(base + o_erv16);
+    D.status = (int32_t*)(base + o_st);
+    P->xp = (double*)(base + o_xp);
+    P->xp32 = (float*)(base + o_xp32);
+    P->upload_ms = now_ms() - t0;
+  }
+  P->host_kept = P->host_only || opt.keep_host;
+  if (!P->host_kept) {  // keep metadata, drop the bulky arrays
+    HostPlan& h = P->host;
+    std::vector<uint16_t>().swap(h.ell_col);
+    std::vector<double>().swap(h.ell_val);
+    std::vector<float>().swap(h.ell_val_f32);
+    std::vector<uint16_t>().swap(h.ell_val_bf16);
+    std::vector<int32_t>().swap(h.er_col);
+    std::vector<double>().swap(h.er_val);
+    std::vector<float>().swap(h.er_val_f32);
+    std::vector<uint16_t>().swap(h.er_val_bf16);
+    std::vector<int32_t>().swap(h.old_to_new);
+  }
+  *out = P.release();
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_destroy(ehyb_plan_t p) {
+  if (!p) return EHYB_OK;
+  ehyb_status_t st = EHYB_OK;
+  if (p->arena || p->hx || !p->ev_pool.empty()) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
+    if (p->arena) cudaFree(p->arena);
+    if (p->hx) cudaFree(p->hx);
+    if (p->hy) cudaFree(p->hy);
+    for (auto& ev : p->ev_pool) {
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+  }
+  delete p;
+  return st;
+}
+
+static ehyb_status_t record_begin(ehyb_plan_t p, cudaStream_t s, std::pair<cudaEvent_t, cudaEvent_t>** slot) {
+  *slot = nullptr;
+  if (!p->prof) return EHYB_OK;
+  if (p->ev_used == p->ev_pool.size()) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    p->ev_pool.emplace_back(a, b);
+  }
+  *slot = &p->ev_pool[p->ev_used++];
+  CK(cudaEventRecord((*slot)->first, s));
+  return EHYB_OK;
+}
+
+static ehyb_status_t record_end(std::pair<cudaEvent_t, cudaEvent_t>* slot, cudaStream_t s) {
+  if (slot) CK(cudaEventRecord(slot->second, s));
+  return EHYB_OK;
+}
+
+static ehyb_status_t check_run(ehyb_plan_t p) {
+  if (!p) return EHYB_ERR_INVALID_ARG;
+  if (p->host_only) return EHYB_ERR_UNSUPPORTED;
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_spmv_permuted(ehyb_plan_t p, const double* xp, double* yp, void* stream) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (p->dev.n == 0) return EHYB_OK;
+  if (!xp || !yp || xp == yp) return EHYB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::pair<cudaEvent_t, cudaEvent_t>* slot;
+  if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
+  CK(launch_ehyb_f64(p->dev, xp, yp, 0, s));
+  return record_end(slot, s);
+}
+
+ehyb_status_t ehyb_spmv(ehyb_plan_t p, const double* x, double* y, void* stream) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (p->dev.n == 0) return EHYB_OK;
+  if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_permute_f64(p->dev, 1, x, p->xp, s));
+  std::pair<cudaEvent_t, cudaEvent_t>* slot;
+  if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
+  CK(launch_ehyb_f64(p->dev, p->xp, y, 1, s));
+  return record_end(slot, s);
+}
+
+ehyb_status_t ehyb_permute(ehyb_plan_t p, int32_t to_new, const double* in, double* out, void* stream) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (p->dev.n == 0) return EHYB_OK;
+  if (!in || !out || in == out) return EHYB_ERR_INVALID_ARG;
+  CK(launch_permute_f64(p->dev, to_new ? 1 : 0, in, out, (cudaStream_t)stream));
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_spmv_host(ehyb_plan_t p, const double* xh, double* yh, void* stream) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (p->dev.n == 0) return EHYB_OK;
+  if (!xh || !yh) return EHYB_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)p->dev.n * sizeof(double);
+  if (!p->hx) {
+    if ((st = dev_alloc((void**)&p->hx, bytes)) != EHYB_OK) return st;
+    if ((st = dev_alloc((void**)&p->hy, bytes)) != EHYB_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(p->hx, xh, bytes, cudaMemcpyHostToDevice, s));
+  if ((st = ehyb_spmv(p, p->hx, p->hy, stream)) != EHYB_OK) return st;
+  CK(cudaMemcpyAsync(yh, p->hy, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t p, const float* x, float* y, void* stream) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (p->lowp == 0) return EHYB_ERR_UNSUPPORTED;
+  if (p->dev.n == 0) return EHYB_OK;
+  if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_permute_f32(p->dev, 1, x, p->xp32, s));
+  std::pair<cudaEvent_t, cudaEvent_t>* slot;
+  if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
+  CK(launch_ehyb_lowp(p->dev, p->lowp, p->xp32, y, 1, s));
+  return record_end(slot, s);
+}
+
+ehyb_status_t ehyb_plan_check(ehyb_plan_t p) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  CK(cudaDeviceSynchronize());
+  int32_t w = 0;
+  CK(cudaMemcpy(&w, p->dev.status, sizeof(w), cudaMemcpyDeviceToHost));
+  if (w) CK(cudaMemset(p->dev.status, 0, sizeof(int32_t)));
+  return (ehyb_status_t)w;
+}
+
+ehyb_status_t ehyb_plan_info(ehyb_plan_t p, ehyb_plan_info_t* info) {
+  if (!p || !info) return EHYB_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  const HostPlan& H = p->host;
+  info->n = H.n;
+  info->nnz = H.nnz;
+  info->nparts = H.nparts;
+  info->nslices = p->nslices;
+  info->slice_rows = p->slice_rows;
+  info->ell_tpr = H.tpr;
+  info->er_tpr = p->er_tpr;
+  info->block_threads = p->dev.threads;
+  info->smem_bytes = (int32_t)ehyb_smem_bytes(p->dev, 8);
+  info->lowp = p->lowp;
+  info->ell_nnz = p->ell_nnz;
+  info->ell_stored = p->ell_stored;
+  info->er_rows = p->er_rows;
+  info->er_nnz = p->er_nnz;
+  info->bytes_effective = p->ell_nnz * 10 + p->er_nnz * 12 + p->er_rows * 8 + H.n * 16;
+  info->bytes_device = (int64_t)p->arena_bytes;
+  info->partition_ms = H.partition_ms;
+  info->reorder_ms = H.reorder_ms;
+  info->upload_ms = p->upload_ms;
+  info->num_sms = p->num_sms;
+  if (!p->host_only) {
+    CK(cudaDeviceSynchronize());
+    int32_t w = 0;
+    CK(cudaMemcpy(&w, p->dev.status, sizeof(w), cudaMemcpyDeviceToHost));
+    info->device_status = w;
+  }
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
+  if (!p || !ex) return EHYB_ERR_INVALID_ARG;
+  HostPlan& H = p->host;
+  if (!p->host_kept && !p->exported) {  // copy the bulky arrays back from the device
+    CK(cudaDeviceSynchronize());
+    try {
+      H.ell_col.resize((size_t)p->ell_stored);
+      H.ell_val.resize((size_t)p->ell_stored);
+      H.er_col.resize((size_t)p->er_nnz);
+      H.er_val.resize((size_t)p->er_nnz);
+    } catch (const std::bad_alloc&) {
+      return EHYB_ERR_OOM;
+    }
+    const DevPlan& D = p->dev;
+    CK(cudaMemcpy(H.ell_col.data(), D.ell_col, H.ell_col.size() * 2, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(H.ell_val.data(), D.ell_val, H.ell_val.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(H.er_col.data(), D.er_col, H.er_col.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(H.er_val.data(), D.er_val, H.er_val.size() * 8, cudaMemcpyDeviceToHost));
+    p->exported = true;
+  }
+  ex->n = H.n;
+  ex->nparts = H.nparts;
+  ex->nslices = H.nslices;
+  ex->tpr = H.tpr;
+  ex->ell_stored = p->ell_stored;
+  ex->er_rows = p->er_rows;
+  ex->er_nnz = p->er_nnz;
+  ex->new_to_old = H.new_to_old.data();
+  ex->part_ptr = H.part_ptr.data();
+  ex->slice_ptr = H.slice_ptr.data();
+  ex->slice_pos = H.slice_pos.data();
+  ex->ell_col = H.ell_col.data();
+  ex->ell_val = H.ell_val.data();
+  ex->row_ell_count = H.row_ell_count.data();
+  ex->er_part_ptr = H.er_part_ptr.data();
+  ex->er_row = H.er_row.data();
+  ex->er_ptr = H.er_ptr.data();
+  ex->er_col = H.er_col.data();
+  ex->er_val = H.er_val.data();
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_profile_enable(ehyb_plan_t p, int32_t enable) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  p->prof = enable != 0;
+  p->ev_used = 0;
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_profile_read(ehyb_plan_t p, double* total_ms, int64_t* launches) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (!total_ms || !launches) return EHYB_ERR_INVALID_ARG;
+  double t = 0;
+  for (size_t i = 0; i < p->ev_used; ++i) {
+    CK(cudaEventSynchronize(p->ev_pool[i].second));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, p->ev_pool[i].first, p->ev_pool[i].second));
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = (int64_t)p->ev_used;
+  return EHYB_OK;
+}
+
+// ---------------------------------------------------------------- CSR baseline
+
+ehyb_status_t ehyb_csr_create(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col, const double* val,
+                              int32_t tpr, void* stream, ehyb_csr_t* out) {
+  if (!out) return EHYB_ERR_INVALID_ARG;
+  *out = nullptr;
+  ehyb_status_t st = validate_csr(n, n, nnz, rp, col, val);
+  if (st != EHYB_OK) return st;
+  if (tpr != 0 && !is_pow2_in(tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
+  DeviceInfo d;
+  if ((st = query_device(d)) != EHYB_OK) return st;
+  std::unique_ptr<ehyb_csr_s> m(new ehyb_csr_s());
+  m->n = n;
+  m->nnz = nnz;
+  m->tpr = tpr ? tpr : pow2_near(n ? std::sqrt((double)nnz / (double)n) : 1.0);
+  if ((st = dev_alloc((void**)&m->rp, (size_t)(n + 1) * 8)) != EHYB_OK) return st;
+  if ((st = dev_alloc((void**)&m->col, (size_t)nnz * 4)) != EHYB_OK) { cudaFree(m->rp); return st; }
+  if ((st = dev_alloc((void**)&m->val, (size_t)nnz * 8)) != EHYB_OK) { cudaFree(m->rp); cudaFree(m->col); return st; }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(m->rp, rp, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(m->col, col, (size_t)nnz * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(m->val, val, (size_t)nnz * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(m->rp); cudaFree(m->col); cudaFree(m->val);
+    return cuda_fail(e, "csr upload");
+  }
+  *out = m.release();
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_csr_spmv(ehyb_csr_t m, const double* x, double* y, void* stream) {
+  if (!m) return EHYB_ERR_INVALID_ARG;
+  if (m->n == 0) return EHYB_OK;
+  if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
+  CK(launch_csr_f64(m->n, m->rp, m->col, m->val, x, y, m->tpr, (cudaStream_t)stream));
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_csr_set_tpr(ehyb_csr_t m, int32_t tpr) {
+  if (!m || !is_pow2_in(tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
+  m->tpr = tpr;
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_csr_destroy(ehyb_csr_t m) {
+  if (!m) return EHYB_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(m->rp);
+  cudaFree(m->col);
+  cudaFree(m->val);
+  delete m;
+  return e == cudaSuccess ? EHYB_OK : cuda_fail(e, "cudaDeviceSynchronize");
+}
+
+}  // extern "C"

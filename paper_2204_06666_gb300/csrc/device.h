@@ -1,0 +1,54 @@
+// Device-side view of a plan and the launch entry points of the SpMV kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ehyb {
+
+// Plan arrays on the device (names after the paper: part_ptr = partBoundary, slice_pos =
+// PositionELL, ell_col = ColELL, ell_val = ValELL, er_row = yIdxER).
+struct DevPlan {
+  int64_t n = 0;
+  int32_t nparts = 0, tpr = 1, er_tpr = 1, threads = 512;
+  int32_t max_part_rows = 0;
+  const int32_t* new_to_old = nullptr;
+  const int32_t* part_ptr = nullptr;
+  const int32_t* slice_ptr = nullptr;
+  const int64_t* slice_pos = nullptr;
+  const uint16_t* ell_col = nullptr;
+  const double* ell_val = nullptr;
+  const float* ell_val_f32 = nullptr;
+  const uint16_t* ell_val_bf16 = nullptr;
+  const int32_t* er_part_ptr = nullptr;
+  const int32_t* er_row = nullptr;
+  const int64_t* er_ptr = nullptr;
+  const int32_t* er_col = nullptr;
+  const double* er_val = nullptr;
+  const float* er_val_f32 = nullptr;
+  const uint16_t* er_val_bf16 = nullptr;
+  int32_t* status = nullptr;  // device status word (first fault wins)
+  uint64_t wait_timeout_ns = 1000000000ull;
+  int32_t inject_wait_fault = 0;
+};
+
+// dynamic shared memory of the fused kernel for an x element of `elem_bytes`
+size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes);
+
+// x_p[i] = x[new_to_old[i]] (to_new) or y[new_to_old[i]] = y_p[i] (!to_new)
+cudaError_t launch_permute_f64(const DevPlan& P, int to_new, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, float* out, cudaStream_t s);
+
+// Fused slab + ER kernel.  xp is in the plan numbering; y is written at new_to_old[r] when
+// scatter != 0, else at r.
+cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s);
+// values stored FP32 (lowp = 1) or BF16 (lowp = 2); x, y and the accumulation in FP32
+cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s);
+
+// plain vector-CSR baseline: tpr lanes per row
+cudaError_t launch_csr_f64(int64_t n, const int64_t* rp, const int32_t* col, const double* val, const double* x,
+                           double* y, int tpr, cudaStream_t s);
+
+// one-time per-device kernel attribute setup (opt-in shared memory)
+cudaError_t kernels_init(int smem_optin);
+
+}  // namespace ehyb

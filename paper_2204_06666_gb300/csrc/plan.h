@@ -1,0 +1,55 @@
+// Host-side EHYB planner: graph partitioning (Sec. 3.1), the cache-size rule (Eq. 1, Eq. 2),
+// the post-partition reordering (Alg. 1) and the slab / extra-rows encoding (Alg. 2).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace ehyb {
+
+struct PlanParams {
+  int64_t n = 0;
+  int32_t slice_rows = 0;     // hard cap on rows per partition (VecSize), resolved before build
+  int32_t ell_width_cap = 0;  // 0 = unlimited
+  int32_t ell_tpr = 1;        // lanes per row in a slab slice
+  int32_t lowp = 0;           // 0 none, 1 fp32, 2 bf16 value copies
+  const int32_t* part_vec = nullptr;
+};
+
+struct HostPlan {
+  int64_t n = 0, nnz = 0;
+  int32_t nparts = 0, nslices = 0, tpr = 1, slice_rows = 0;
+  std::vector<int32_t> new_to_old, old_to_new;
+  std::vector<int32_t> part_ptr, slice_ptr;
+  std::vector<int64_t> slice_pos;
+  std::vector<uint16_t> ell_col;
+  std::vector<double> ell_val;
+  std::vector<float> ell_val_f32;
+  std::vector<uint16_t> ell_val_bf16;
+  std::vector<int32_t> row_ell_count;
+  std::vector<int32_t> er_part_ptr, er_row;
+  std::vector<int64_t> er_ptr;
+  std::vector<int32_t> er_col;
+  std::vector<double> er_val;
+  std::vector<float> er_val_f32;
+  std::vector<uint16_t> er_val_bf16;
+  int64_t ell_nnz = 0;
+  int32_t max_part_rows = 0;
+  double partition_ms = 0, reorder_ms = 0;
+};
+
+// Eq. 1 and Eq. 2: smallest K >= 1 with n*tau/(K*P) < budget (and at most 2^16 rows so the
+// 16-bit column offset holds); returns VecSize = ceil(n / (K*P)).
+int32_t eq1_slice_rows(int64_t n, int tau, int P, int64_t budget_bytes);
+
+// Partition the symmetrised graph of A (pattern of A + A^T, no self loops) into parts of at most
+// `cap` vertices by greedy graph growing; returns the number of parts.
+int32_t partition_graph(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t cap,
+                        std::vector<int32_t>& part);
+
+// 0 on success, else an ehyb_status_t code (validation is done by the caller).
+int build_plan(const PlanParams& prm, const int64_t* row_ptr, const int32_t* col, const double* val,
+               HostPlan& out);
+
+uint16_t f32_to_bf16_rne(float f);
+
+}  // namespace ehyb

@@ -1,0 +1,360 @@
+// EHYB SpMV kernels for sm_103a.
+//
+// ehyb_kernel: Alg. 3 re-designed for GB300.  One thread block per partition (the paper's
+//   "block = partition", Sec. 3.2):
+//     1. thread 0 issues ONE bulk asynchronous copy (cp.async.bulk, completion counted on an
+//        mbarrier) of the partition's slice of x into shared memory: CachedVec of Alg. 3;
+//        a ragged unaligned tail (at most 15 bytes) is fetched with plain loads;
+//     2. thread 0 waits on the mbarrier with a time bound (on expiry the block records
+//        EHYB_ERR_TIMEOUT in the plan status word and returns);
+//     3. each warp takes 32-lane slices of the partition from a shared counter (the dynamic
+//        slice balancing of Alg. 3) and runs y[row] = sum_k ValELL * CachedVec[ColELL] with the
+//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot;
+//     4. after a block barrier the same block adds the ER lines of its own rows
+//        (extra entries, global gathers of x, er_tpr lanes per line + shuffle reduction),
+//        y[yIdxER] += sum, so that the result is ell_sum + er_sum for every row, deterministic.
+//   The paper's second pass over ER slices from a global counter is folded into step 4: the
+//   rows a block updates are its own, so no atomics and no second launch are needed.
+//
+// csr_kernel: the plain vector-CSR baseline (Bell & Garland, Sec. 2.2), tpr lanes per row.
+#include "device.h"
+
+#include <cstdint>
+
+namespace ehyb {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kTimeoutCode = 9;  // EHYB_ERR_TIMEOUT
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: true when phase `parity` completed within limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float(((uint32_t)h) << 16); }
+
+template <typename V, typename X>
+__device__ __forceinline__ X load_val(const V* p);
+template <>
+__device__ __forceinline__ double load_val<double, double>(const double* p) {
+  return __ldcs(p);
+}
+template <>
+__device__ __forceinline__ float load_val<float, float>(const float* p) {
+  return __ldcs(p);
+}
+template <>
+__device__ __forceinline__ float load_val<uint16_t, float>(const uint16_t* p) {
+  return bf16_to_f32(__ldcs(reinterpret_cast<const unsigned short*>(p)));
+}
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+struct KArgs {
+  int32_t tpr_log2, er_tpr_log2;
+  const int32_t* new_to_old;
+  const int32_t* part_ptr;
+  const int32_t* slice_ptr;
+  const int64_t* slice_pos;
+  const uint16_t* ell_col;
+  const int32_t* er_part_ptr;
+  const int32_t* er_row;
+  const int64_t* er_ptr;
+  const int32_t* er_col;
+  int32_t* status;
+  uint64_t timeout_ns;
+  int32_t inject;
+};
+
+// V: stored value type; X: type of x, y and of the accumulation
+template <typename V, typename X, bool SCATTER>
+__global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
+                                                    const V* __restrict__ er_val, const X* __restrict__ xp,
+                                                    X* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int slice_counter;
+  __shared__ int stage_ok;
+  constexpr int EPV = 16 / (int)sizeof(X);  // elements per 16 bytes
+
+  const int p = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int pb = a.part_ptr[p];
+  const int pe = a.part_ptr[p + 1];
+  const int s0 = a.slice_ptr[p];
+  const int s1 = a.slice_ptr[p + 1];
+
+  // ---- 1. stage x_p[pb, pe) into shared memory
+  const int a0 = pb & ~(EPV - 1);  // 16-byte aligned start
+  const int a1 = pe & ~(EPV - 1);  // bulk part ends at the last aligned boundary <= pe
+  X* xs = reinterpret_cast<X*>(smem_raw);
+  const bool aligned_src = ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
+  const uint32_t bulk_bytes = (aligned_src && a1 > a0) ? (uint32_t)(a1 - a0) * (uint32_t)sizeof(X) : 0u;
+  if (tid == 0) {
+    slice_counter = s0 + nwarps;
+    if (bulk_bytes) {
+      mbar_init(&bar, 1);
+      mbar_arrive_expect_tx(&bar, bulk_bytes);
+      if (!a.inject) bulk_g2s(xs, xp + a0, bulk_bytes, &bar);
+    }
+  }
+  // plain loads: everything when the source is unaligned, else the ragged tail [a1, pe)
+  {
+    const int lo = bulk_bytes ? (a1 > pb ? a1 : pb) : pb;
+    for (int i = lo + tid; i < pe; i += blockDim.x) xs[i - a0] = xp[i];
+  }
+  if (tid == 0) {
+    int ok = 1;
+    if (bulk_bytes) {
+      ok = mbar_wait_bounded(&bar, 0, a.timeout_ns) ? 1 : 0;
+      if (!ok) {
+        atomicCAS(a.status, 0, kTimeoutCode);
+        // a copy that was issued must land before the block's shared memory goes away
+        if (!a.inject) mbar_wait_bounded(&bar, 0, a.timeout_ns);
+      }
+    }
+    stage_ok = ok;
+  }
+  __syncthreads();
+  if (!stage_ok) return;
+  // every thread observes the completed phase itself (acquire of the bulk-copy writes)
+  if (bulk_bytes) (void)mbar_try_wait(&bar, 0);
+
+  const X* xsl = xs + (pb - a0);  // xsl[local column] = x_p[pb + local column]
+  const int tpr = 1 << a.tpr_log2;
+  const int sub = lane & (tpr - 1);
+  const int rows_per_slice = 32 >> a.tpr_log2;
+
+  // ---- 2. slab: warp per 32-lane slice, dynamic slice balancing inside the partition
+  int s = s0 + warp;
+  while (s < s1) {
+    const int64_t pos = a.slice_pos[s];
+    const int w = (int)((a.slice_pos[s + 1] - pos) >> 5);
+    const V* vp = ell_val + pos + lane;
+    const uint16_t* cp = a.ell_col + pos + lane;
+    X acc = X(0);
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const X v = load_val<V, X>(vp + 32 * (int64_t)k);
+      const int c = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)k));
+      acc = fma_t(v, xsl[c], acc);
+    }
+    for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
+    if (sub == 0 && row < pe) {
+      if (SCATTER) y[a.new_to_old[row]] = acc;
+      else y[row] = acc;
+    }
+    int nxt = 0;
+    if (lane == 0) nxt = atomicAdd(&slice_counter, 1);
+    s = __shfl_sync(FULL, nxt, 0);
+  }
+  const int e0 = a.er_part_ptr[p];
+  const int e1 = a.er_part_ptr[p + 1];
+  if (e0 == e1) return;
+  __syncthreads();  // slab results of this block are visible before the ER updates
+
+  // ---- 3. ER lines of this partition: er_tpr lanes per line, shuffle reduction
+  const int etpr = 1 << a.er_tpr_log2;
+  const int esub = lane & (etpr - 1);
+  const int lines_per_warp = 32 >> a.er_tpr_log2;
+  for (int eb = e0 + warp * lines_per_warp; eb < e1; eb += nwarps * lines_per_warp) {
+    const int e = eb + (lane >> a.er_tpr_log2);
+    X acc = X(0);
+    if (e < e1) {
+      const int64_t k1 = a.er_ptr[e + 1];
+      for (int64_t k = a.er_ptr[e] + esub; k < k1; k += etpr)
+        acc = fma_t(load_val<V, X>(er_val + k), __ldg(xp + __ldcs(a.er_col + k)), acc);
+    }
+    for (int off = etpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if (esub == 0 && e < e1) {
+      const int row = a.er_row[e];
+      if (SCATTER) y[a.new_to_old[row]] += acc;
+      else y[row] += acc;
+    }
+  }
+}
+
+template <typename X>
+__global__ void permute_kernel(int64_t n, const int32_t* __restrict__ n2o, int to_new, const X* __restrict__ in,
+                               X* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (to_new) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = __ldg(in + n2o[i]);
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[n2o[i]] = in[i];
+  }
+}
+
+__global__ void csr_kernel(int64_t n, int tpr_log2, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = t >> tpr_log2;
+  const int tpr = 1 << tpr_log2;
+  const int sub = (int)(t & (tpr - 1));
+  double acc = 0.0;
+  if (row < n) {
+    const int64_t k1 = rp[row + 1];
+    for (int64_t k = rp[row] + sub; k < k1; k += tpr) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(col + k)), acc);
+  }
+  for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+  if (sub == 0 && row < n) y[row] = acc;
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << (l + 1)) <= v) ++l;
+  return l;
+}
+
+KArgs make_args(const DevPlan& P) {
+  KArgs a;
+  a.tpr_log2 = ilog2(P.tpr);
+  a.er_tpr_log2 = ilog2(P.er_tpr);
+  a.new_to_old = P.new_to_old;
+  a.part_ptr = P.part_ptr;
+  a.slice_ptr = P.slice_ptr;
+  a.slice_pos = P.slice_pos;
+  a.ell_col = P.ell_col;
+  a.er_part_ptr = P.er_part_ptr;
+  a.er_row = P.er_row;
+  a.er_ptr = P.er_ptr;
+  a.er_col = P.er_col;
+  a.status = P.status;
+  a.timeout_ns = P.wait_timeout_ns;
+  a.inject = P.inject_wait_fault;
+  return a;
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes) {
+  const int epv = 16 / elem_bytes;
+  size_t b = (size_t)(P.max_part_rows + epv) * (size_t)elem_bytes;
+  return (b + 15) & ~(size_t)15;
+}
+
+cudaError_t kernels_init(int smem_optin) {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(ehyb_kernel<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ehyb_kernel<double, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ehyb_kernel<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ehyb_kernel<float, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ehyb_kernel<uint16_t, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(ehyb_kernel<uint16_t, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin);
+}
+
+cudaError_t launch_permute_f64(const DevPlan& P, int to_new, const double* in, double* out, cudaStream_t s) {
+  if (P.n == 0) return cudaSuccess;
+  permute_kernel<double><<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.new_to_old, to_new, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, float* out, cudaStream_t s) {
+  if (P.n == 0) return cudaSuccess;
+  permute_kernel<float><<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.new_to_old, to_new, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s) {
+  if (P.nparts == 0) return cudaSuccess;
+  const size_t smem = ehyb_smem_bytes(P, 8);
+  KArgs a = make_args(P);
+  if (scatter) ehyb_kernel<double, double, true><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val, P.er_val, xp, y);
+  else ehyb_kernel<double, double, false><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val, P.er_val, xp, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s) {
+  if (P.nparts == 0) return cudaSuccess;
+  const size_t smem = ehyb_smem_bytes(P, 4);
+  KArgs a = make_args(P);
+  if (lowp == 1) {
+    if (scatter) ehyb_kernel<float, float, true><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_f32, P.er_val_f32, xp, y);
+    else ehyb_kernel<float, float, false><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_f32, P.er_val_f32, xp, y);
+  } else {
+    if (scatter)
+      ehyb_kernel<uint16_t, float, true><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_bf16, P.er_val_bf16, xp, y);
+    else
+      ehyb_kernel<uint16_t, float, false><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_bf16, P.er_val_bf16, xp, y);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_f64(int64_t n, const int64_t* rp, const int32_t* col, const double* val, const double* x,
+                           double* y, int tpr, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t total = n * (int64_t)tpr;
+  const int64_t blocks = (total + threads - 1) / threads;
+  csr_kernel<<<(unsigned)blocks, threads, 0, s>>>(n, ilog2(tpr), rp, col, val, x, y);
+  return cudaGetLastError();
+}
+
+}  // namespace ehyb

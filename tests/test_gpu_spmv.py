@@ -1,0 +1,238 @@
+"""GPU parity of the EHYB SpMV (C ABI) against the CPU oracle.
+
+Bars: bit-exact on integer-valued inputs (every partial sum is an exact integer in FP64, so the
+summation order cannot matter); on FEM inputs rel-L2 <= 1e-13 AND, row by row,
+|y_gpu - y_oracle| <= 2 gamma_{k+6} (|A||x|)_i with u = 2^-53 -- the recursive-summation bound of
+both sides (k = row length; +6 covers the shuffle-reduction depth and the slab + ER combination).
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eh():
+    import paper_2204_06666_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _run(eh, A, x, **opt):
+    P = eh.Plan(A, **opt)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    yd = torch.full_like(xd, np.nan)
+    P.spmv(xd, yd)
+    torch.cuda.synchronize()
+    assert P.check() == 0
+    return P, yd.cpu().numpy()
+
+
+def _row_bound(A, x):
+    k = np.diff(A.row_ptr).astype(np.float64)
+    return 2 * oracle.gamma(k + 6) * oracle.abs_spmv(A, x)
+
+
+def _check_fp(A, x, y):
+    ref = oracle.spmv(A, x)
+    err = np.linalg.norm(y - ref) / max(np.linalg.norm(ref), 1e-300)
+    assert err <= 1e-13, err
+    assert np.all(np.abs(y - ref) <= _row_bound(A, x)), np.max(np.abs(y - ref) - _row_bound(A, x))
+    return err
+
+
+OPTS = [dict(), dict(ell_tpr=2, er_tpr=1), dict(ell_tpr=4, er_tpr=32), dict(ell_tpr=32, er_tpr=8),
+        dict(ell_width_cap=6, er_tpr=4), dict(slice_rows=37, block_threads=64), dict(slice_rows=1),
+        dict(slice_rows=2000, block_threads=1024), dict(slice_rows=33, block_threads=32)]
+
+
+@pytest.mark.parametrize("opt", OPTS)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_integer_bit_exact_ragged(eh, opt, seed):
+    A = gen.random_csr(3001 + seed, seed, mean_row=11, int_values=True, empty_frac=0.05, long_rows=5,
+                       long_len=1500, duplicates=True)
+    x = gen.int_vector(A.n, seed + 100)
+    _, y = _run(eh, A, x, **opt)
+    assert np.array_equal(y, oracle.spmv(A, x))
+
+
+@pytest.mark.parametrize("name,N,slice_rows", [("fem2d", 200, 0), ("hex", 16, 0), ("hex", 16, 700),
+                                               ("tet", 20, 0), ("tet", 20, 1000)])
+def test_fem_parity(eh, name, N, slice_rows):
+    A = {"fem2d": gen.fem2d_p1, "hex": gen.hex_elast3d, "tet": gen.tet_lap3d}[name](N=N)
+    x = gen.uniform(A.n, 13)
+    _, y = _run(eh, A, x, slice_rows=slice_rows)
+    _check_fp(A, x, y)
+
+
+def test_hex70_full_size_as_benchmarked(eh):
+    # the benchmarked workload, default plan (Eq. 1) and launch configuration
+    A = gen.hex_elast3d()
+    x = gen.uniform(A.n, 13)
+    P, y = _run(eh, A, x)
+    err = _check_fp(A, x, y)
+    info = P.info()
+    assert info["nparts"] == 152 and info["device_status"] == 0
+    # run-to-run bit reproducibility
+    xd = torch.from_numpy(x).cuda()
+    y2 = torch.empty_like(xd)
+    for _ in range(3):
+        P.spmv(xd, y2)
+    torch.cuda.synchronize()
+    assert np.array_equal(y2.cpu().numpy(), y)
+    assert err <= 1e-13
+
+
+def test_tet126_full_size(eh):
+    A = gen.tet_lap3d()
+    x = gen.uniform(A.n, 23)
+    _, y = _run(eh, A, x)
+    _check_fp(A, x, y)
+
+
+def test_permuted_entry_and_permute(eh):
+    A = gen.hex_elast3d(N=10)
+    x = gen.uniform(A.n, 5)
+    P, y = _run(eh, A, x, slice_rows=500)
+    n2o = P.export()["new_to_old"]
+    xd = torch.from_numpy(x).cuda()
+    xp = torch.empty_like(xd)
+    P.permute(True, xd, xp)
+    assert np.array_equal(xp.cpu().numpy(), x[n2o])
+    yp = torch.empty_like(xd)
+    P.spmv_permuted(xp, yp)
+    back = torch.empty_like(xd)
+    P.permute(False, yp, back)
+    torch.cuda.synchronize()
+    assert np.array_equal(back.cpu().numpy(), y)
+    # an x that is not 16-byte aligned takes the plain-load staging path and gives the same bits
+    big = torch.zeros(A.n + 1, dtype=torch.float64, device="cuda")
+    big[1:] = xp
+    yp2 = torch.empty_like(xd)
+    P.spmv_permuted(big[1:], yp2)
+    torch.cuda.synchronize()
+    assert np.array_equal(yp2.cpu().numpy(), yp.cpu().numpy())
+
+
+def test_host_entry_matches_device_entry(eh):
+    A = gen.fem2d_p1(N=80)
+    x = gen.uniform(A.n, 9)
+    P, y = _run(eh, A, x)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    P.spmv_host(xh, yh)
+    assert np.array_equal(yh.numpy(), y)
+    yn = np.zeros(A.n)
+    P.spmv_host(np.ascontiguousarray(x), yn)   # pageable numpy buffers work too
+    assert np.array_equal(yn, y)
+
+
+@pytest.mark.parametrize("lowp", [1, 2])
+def test_lowp_integer_exact_and_fem_bound(eh, lowp):
+    A = gen.random_csr(2000, 4, mean_row=12, int_values=True, empty_frac=0.05, long_rows=2, long_len=600)
+    x = gen.int_vector(A.n, 6)
+    P = eh.Plan(A, lowp=lowp, slice_rows=300)
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    yd = torch.empty_like(xd)
+    P.spmv_lowp(xd, yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(yd.cpu().numpy().astype(np.float64), oracle.spmv(A, x))
+    B = gen.tet_lap3d(N=20)
+    xb = gen.uniform(B.n, 3)
+    P = eh.Plan(B, lowp=lowp)
+    xd = torch.from_numpy(xb.astype(np.float32)).cuda()
+    yd = torch.empty_like(xd)
+    P.spmv_lowp(xd, yd)
+    torch.cuda.synchronize()
+    ref = oracle.spmv_low(B, xb, bf16=(lowp == 2))
+    k = np.diff(B.row_ptr).astype(np.float64)
+    bound = 2 * oracle.gamma(k + 6, 2.0 ** -24) * oracle.abs_spmv(B, xb)
+    assert np.all(np.abs(yd.cpu().numpy() - ref) <= bound)
+
+
+def test_lowp_requires_lowp_plan(eh):
+    A = gen.fem2d_p1(N=20)
+    P = eh.Plan(A)
+    x = torch.zeros(A.n, dtype=torch.float32, device="cuda")
+    with pytest.raises(eh.EhybError) as e:
+        P.spmv_lowp(x, torch.empty_like(x))
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("tpr", [1, 2, 4, 8, 32])
+def test_csr_baseline_parity(eh, tpr):
+    A = gen.random_csr(2500, 8, mean_row=10, int_values=True, empty_frac=0.05, long_rows=3, long_len=900,
+                       duplicates=True)
+    x = gen.int_vector(A.n, 1)
+    M = eh.CsrBaseline(A, tpr=tpr)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    M.spmv(xd, yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(yd.cpu().numpy(), oracle.spmv(A, x))
+    B = gen.hex_elast3d(N=12)
+    xb = gen.uniform(B.n, 2)
+    M = eh.CsrBaseline(B, tpr=tpr)
+    xd = torch.from_numpy(xb).cuda()
+    yd = torch.empty_like(xd)
+    M.spmv(xd, yd)
+    torch.cuda.synchronize()
+    _check_fp(B, xb, yd.cpu().numpy())
+
+
+def test_edge_cases(eh):
+    for n in (1, 2, 31, 32, 33, 65):
+        A = gen.random_csr(n, n, mean_row=3, int_values=True, empty_frac=0.3)
+        x = gen.int_vector(n, n)
+        _, y = _run(eh, A, x, slice_rows=16)
+        assert np.array_equal(y, oracle.spmv(A, x)), n
+    Z = gen.CSR(40, np.zeros(41, np.int64), np.zeros(0, np.int32), np.zeros(0))   # no entries at all
+    _, y = _run(eh, Z, np.ones(40))
+    assert np.all(y == 0)
+    E = gen.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    P = eh.Plan(E)
+    P.spmv(torch.zeros(1, dtype=torch.float64, device="cuda")[:0], torch.zeros(1, dtype=torch.float64, device="cuda")[:0])
+    assert P.check() == 0
+
+
+def test_staging_wait_timeout_is_reported_and_context_survives(eh):
+    A = gen.fem2d_p1(N=30)
+    x = gen.uniform(A.n, 1)
+    # the wait is given a copy that is never issued: it must run out after 2 ms and report
+    P = eh.Plan(A, slice_rows=100, inject_wait_fault=1, wait_timeout_ns=2_000_000)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    P.spmv(xd, yd)
+    assert P.check() == eh.EHYB_ERR_TIMEOUT
+    assert P.check() == 0   # reading clears the word
+    # the context is intact: a normal plan still computes correctly
+    Q, y = _run(eh, A, x, slice_rows=100)
+    _check_fp(A, x, y)
+
+
+def test_oom_hook(eh):
+    A = gen.fem2d_p1(N=30)
+    eh.ehyb_test_fail_allocs_after(0)
+    try:
+        with pytest.raises(eh.EhybError) as e:
+            eh.Plan(A)
+        assert e.value.status == 5
+    finally:
+        eh.ehyb_test_fail_allocs_after(-1)
+    eh.Plan(A)
+
+
+def test_profile_counts_main_kernel(eh):
+    A = gen.fem2d_p1(N=50)
+    P = eh.Plan(A)
+    xd = torch.from_numpy(gen.uniform(A.n, 1)).cuda()
+    yd = torch.empty_like(xd)
+    P.profile_enable(True)
+    for _ in range(5):
+        P.spmv(xd, yd)
+    ms, cnt = P.profile_read()
+    assert cnt == 5 and ms > 0

@@ -1,0 +1,117 @@
+"""Host planner (Alg. 1 / Alg. 2, Eq. 1, partitioner) checked on the CPU against the independent decoder."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import ehyb_format as ef
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ehyb_tiny.json")
+
+
+def _plan(A, **kw):
+    import paper_2204_06666_gb300 as eh
+    return eh.Plan(A, host_only=1, **kw)
+
+
+def test_golden_plan_matches_hand_derivation_exactly():
+    g = json.load(open(GOLDEN))
+    A = gen.CSR(g["n"], np.array(g["row_ptr"], np.int64), np.array(g["col"], np.int32), np.array(g["val"], float))
+    ex = _plan(A, part_vec=g["part_vec"]).export()
+    for k in ("new_to_old", "part_ptr", "slice_ptr", "slice_pos", "row_ell_count", "er_row", "er_ptr", "er_col"):
+        assert list(ex[k]) == g["plan"][k], k
+    assert list(ex["er_val"]) == g["plan"]["er_val"]
+    want_col = np.zeros(g["plan"]["slice_pos"][-1], np.uint16)
+    want_val = np.zeros(g["plan"]["slice_pos"][-1])
+    for pos, c, v in g["plan"]["ell_entries"]:
+        want_col[pos], want_val[pos] = c, v
+    assert np.array_equal(ex["ell_col"], want_col) and np.array_equal(ex["ell_val"], want_val)
+
+
+def _invariants(A, ex, cap=None, width_cap=0):
+    n = A.n
+    n2o = ex["new_to_old"]
+    assert np.array_equal(np.sort(n2o), np.arange(n))                    # a permutation
+    o2n = np.empty(n, np.int64)
+    o2n[n2o] = np.arange(n)
+    assert np.array_equal(n2o[o2n], np.arange(n))                        # round trip, bit-exact
+    pp = ex["part_ptr"]
+    sizes = np.diff(pp)
+    assert pp[0] == 0 and pp[-1] == n and np.all(sizes >= 0)
+    if cap:
+        assert sizes.max(initial=0) <= cap
+    cnt = ex["row_ell_count"]
+    er_cnt = np.zeros(n, np.int64)
+    er_cnt[ex["er_row"]] = np.diff(ex["er_ptr"])
+    for p in range(len(pp) - 1):
+        c = cnt[pp[p]:pp[p + 1]]
+        assert np.all(np.diff(c) <= 0)                                   # Alg. 1: descending within a partition
+        e0, e1 = ex["er_part_ptr"][p], ex["er_part_ptr"][p + 1]
+        rows = ex["er_row"][e0:e1]
+        assert np.all((rows >= pp[p]) & (rows < pp[p + 1]))              # ER lines owned by their partition
+        assert np.all(np.diff(er_cnt[rows]) <= 0)                        # ER lines by count, descending
+        ns = ex["slice_ptr"][p + 1] - ex["slice_ptr"][p]
+        assert ns == -(-(pp[p + 1] - pp[p]) // (32 // ex["tpr"]))         # slices never straddle partitions
+    assert np.all(ex["ell_col"].astype(np.int64) < np.maximum(1, sizes.max(initial=1)))
+    if width_cap:
+        assert cnt.max(initial=0) <= width_cap
+    assert np.array_equal(np.sort(np.unique(ex["er_row"])), np.sort(ex["er_row"]))  # one line per row
+    assert np.all(np.diff(ex["slice_pos"]) % 32 == 0)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(ell_tpr=2), dict(ell_tpr=4, er_tpr=8), dict(ell_tpr=32),
+                                dict(ell_width_cap=5), dict(slice_rows=37), dict(slice_rows=1),
+                                dict(lowp=1), dict(lowp=2)])
+def test_decode_multiset_random_ragged(kw):
+    A = gen.random_csr(700, 7, mean_row=9, empty_frac=0.1, long_rows=3, long_len=400, duplicates=True)
+    ex = _plan(A, **kw).export()
+    assert ef.same_multiset(ef.decode(ex), ef.triplets(A))
+    _invariants(A, ex, cap=kw.get("slice_rows"), width_cap=kw.get("ell_width_cap", 0))
+
+
+@pytest.mark.parametrize("name", ["fem2d", "hex", "tet"])
+def test_decode_multiset_fem(name):
+    A = {"fem2d": lambda: gen.fem2d_p1(N=40), "hex": lambda: gen.hex_elast3d(N=8),
+         "tet": lambda: gen.tet_lap3d(N=12)}[name]()
+    P = _plan(A, slice_rows=200)
+    ex = P.export()
+    assert ef.same_multiset(ef.decode(ex), ef.triplets(A))
+    _invariants(A, ex, cap=200)
+    info = P.info()
+    assert info["ell_nnz"] + info["er_nnz"] == A.nnz
+    assert info["nparts"] == -(-A.n // 200)     # parts are filled to the cap
+
+
+def test_eq1_default_matches_oracle_rule():
+    for N, sms in ((200, 152), (70, 152), (30, 80)):
+        A = gen.fem2d_p1(N=N) if N != 70 else gen.hex_elast3d(N=12)
+        info = _plan(A, num_sms=sms).info()
+        K, vec = ef.eq1(A.n, 8, sms, 232448 - 1024 - 32)
+        assert info["slice_rows"] == vec and info["nparts"] == -(-A.n // vec)
+
+
+def test_edge_sizes():
+    for n in (0, 1, 2, 31, 33):
+        A = gen.random_csr(n, 3, mean_row=2, empty_frac=0.3)
+        ex = _plan(A, slice_rows=16).export()
+        assert ef.same_multiset(ef.decode(ex), ef.triplets(A))
+    Z = gen.CSR(5, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    info = _plan(Z).info()
+    assert info["ell_nnz"] == 0 and info["er_nnz"] == 0
+
+
+def test_partition_quality_3d_hex():
+    # a cube of ~13^3 nodes loses ~14.6% of the 27-point couplings across its faces; the in-house
+    # partitioner must come close (measured quality, not a parity pin)
+    A = gen.hex_elast3d(N=30)
+    info = _plan(A, slice_rows=6770).info()
+    assert info["er_nnz"] / A.nnz < 0.25
+
+
+def test_footprint_model_matches_sec_3_4():
+    A = gen.fem2d_p1(N=50)
+    info = _plan(A).info()
+    n = A.n
+    assert info["bytes_effective"] == 10 * info["ell_nnz"] + 12 * info["er_nnz"] + 8 * info["er_rows"] + 16 * n
