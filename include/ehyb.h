@@ -151,6 +151,19 @@ ehyb_status_t ehyb_permute(ehyb_plan_t plan, int32_t to_new, const double* in, d
  */
 ehyb_status_t ehyb_spmv_host(ehyb_plan_t plan, const double* x_host, double* y_host, void* stream);
 
+/*
+ * y = A x exactly as ehyb_spmv computes it, for callers that cannot allocate device memory when
+ * they call (a plug-in whose host framework owns all device memory, a latency-critical loop, a
+ * thread holding a lock the allocator needs).  The paper has no counterpart: this is a library
+ * convenience.  Instead of the plan's workspace, the gathered copy of x goes to a fixed 8 MiB
+ * array compiled into the library (present on every GPU that loads it, until exit), so the plan
+ * may have at most 2^20 rows (EHYB_ERR_TOO_LARGE otherwise).  The call allocates nothing.  The
+ * first call on a device looks the array's device address up once, with that device current;
+ * make that first call before any stream capture.  All calls share the array: calls that overlap
+ * in time on the GPU (other streams, other threads) race on it; each call rewrites what it reads.
+ */
+ehyb_status_t ehyb_spmv_noalloc(ehyb_plan_t plan, const double* x, double* y, void* stream);
+
 /* y = A_low x in FP32 arithmetic with values stored as opt.lowp (FP32 or BF16), x and y float
  * device arrays in the original numbering.  EHYB_ERR_UNSUPPORTED if the plan has no lowp copy. */
 ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t plan, const float* x, float* y, void* stream);

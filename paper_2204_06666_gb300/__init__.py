@@ -87,6 +87,7 @@ _sig("ehyb_spmv_permuted", [_P, _P, _P, _P])
 _sig("ehyb_permute", [_P, _I32, _P, _P, _P])
 _sig("ehyb_spmv_host", [_P, _P, _P, _P])
 _sig("ehyb_spmv_lowp", [_P, _P, _P, _P])
+_sig("ehyb_spmv_noalloc", [_P, _P, _P, _P])
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
@@ -174,6 +175,10 @@ def ehyb_spmv_lowp(plan, x, y, stream):
     return _lib.ehyb_spmv_lowp(plan, x, y, stream)
 
 
+def ehyb_spmv_noalloc(plan, x, y, stream):
+    return _lib.ehyb_spmv_noalloc(plan, x, y, stream)
+
+
 def ehyb_plan_check(plan):
     return _lib.ehyb_plan_check(plan)
 
@@ -239,6 +244,10 @@ class Plan:
 
     def spmv_lowp(self, x, y, stream=None):
         _check(ehyb_spmv_lowp(self._h, _dev(x, "float32"), _dev(y, "float32"), _stream(stream)), "ehyb_spmv_lowp")
+
+    def spmv_noalloc(self, x, y, stream=None):
+        _check(ehyb_spmv_noalloc(self._h, _dev(x, "float64"), _dev(y, "float64"), _stream(stream)),
+               "ehyb_spmv_noalloc")
 
     def check(self) -> int:
         return int(ehyb_plan_check(self._h))

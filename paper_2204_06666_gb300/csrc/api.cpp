@@ -148,6 +148,15 @@ struct ehyb_csr_s {
   double* val = nullptr;
 };
 
+namespace ehyb {
+// device view of a plan for entry points defined in other translation units
+const DevPlan* plan_device_view(ehyb_plan_t plan, int* device) {
+  if (!plan || plan->host_only) return nullptr;
+  if (device) *device = plan->device;
+  return &plan->dev;
+}
+}  // namespace ehyb
+
 extern "C" {
 
 const char* ehyb_status_string(ehyb_status_t s) {
