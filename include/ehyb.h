@@ -65,7 +65,8 @@ typedef struct {
   int32_t ell_width_cap;     /* max in-partition entries per row kept in the slab (rest -> ER); 0 = no cap */
   int32_t ell_tpr;           /* lanes per row inside a 32-lane slab slice: 1,2,4,8,16,32; 0 = 1 */
   int32_t er_tpr;            /* lanes per ER line (shuffle-reduced): 1,2,4,8,16,32; 0 = auto */
-  int32_t block_threads;     /* threads per block (multiple of 32, <= 1024); 0 = 512 */
+  int32_t block_threads;     /* threads per block (multiple of 32, <= 1024); 0 = auto (enough warps for the
+                                average partition's slices, 128..1024) */
   int32_t lowp;              /* also store values as EHYB_F32 (1) or EHYB_BF16 (2) for the FP32 kernels; 0 = no */
   int32_t host_only;         /* 1: build the format on the host only (inspection, no GPU use) */
   int32_t num_sms;           /* P of Eq. 1 for host-only plans; 0 = query the current device */
@@ -75,6 +76,8 @@ typedef struct {
   int32_t inject_wait_fault; /* test hook: the staging wait waits for a copy that is never issued */
   int32_t keep_host;         /* keep host copies of the plan arrays (ehyb_plan_export without device reads) */
   uint64_t seed;             /* reserved for randomised partitioners; the in-house one is deterministic */
+  int32_t er_layout;         /* extra rows: 0 = sliced with the slab's own slices (one pass per slice, default),
+                                1 = CSR lines, er_tpr lanes each with a shuffle reduction, after a block barrier */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;
@@ -91,6 +94,8 @@ typedef struct {
   double partition_ms, reorder_ms, upload_ms;
   int32_t device_status;     /* EHYB_OK or the first fault recorded by a kernel */
   int32_t num_sms;
+  int32_t er_layout;         /* as ehyb_options_t.er_layout */
+  int64_t er_stored;         /* sliced layout: ER slots including padding (CSR layout: er_nnz) */
 } ehyb_plan_info_t;
 
 /* Pointers into arrays owned by the plan (valid until ehyb_destroy); see ehyb_plan_export. */
@@ -110,6 +115,14 @@ typedef struct {
   const int64_t* er_ptr;         /* [er_rows+1]: CSR offsets of the ER lines */
   const int32_t* er_col;         /* [er_nnz]: new-numbering column */
   const double* er_val;          /* [er_nnz] */
+  /* er_layout 0 (the CSR arrays above are then empty): ER slots of slab slice s at
+   * er_slice_pos[s] + 32 k + lane, same lane -> row map as the slab, new-numbering columns */
+  int32_t er_layout;
+  int64_t er_stored;
+  const int64_t* er_slice_pos;   /* [nslices+1] */
+  const int32_t* er_scol;        /* [er_stored] (padding: first row of the partition, value 0) */
+  const double* er_sval;         /* [er_stored] */
+  const int32_t* row_er_count;   /* [n]: extra entries of each new row */
 } ehyb_plan_export_t;
 
 const char* ehyb_status_string(ehyb_status_t s);

@@ -44,8 +44,9 @@ def decode(ex: dict):
     """Triplets (rows, cols, vals) in the original numbering, ELL entries first then ER.
 
     ``ex`` holds the exported plan arrays: n, tpr (lanes per row in a slice), new_to_old,
-    part_ptr, slice_ptr, slice_pos, ell_col (uint16), ell_val, row_ell_count (per new row),
-    er_row, er_ptr, er_col, er_val.
+    part_ptr, slice_ptr, slice_pos, ell_col (uint16), ell_val, row_ell_count (per new row), and the
+    extra rows either as CSR lines (er_layout 1: er_row, er_ptr, er_col, er_val) or sliced like the
+    slab (er_layout 0: er_slice_pos, er_scol, er_sval, row_er_count).
     """
     n = int(ex["n"])
     tpr = int(ex["tpr"])
@@ -80,15 +81,38 @@ def decode(ex: dict):
                     rows.append(n2o[row])
                     cols.append(n2o[pb + local])
                     vals.append(ell_val[e])
-    er_row = np.asarray(ex["er_row"], np.int64)
-    er_ptr = np.asarray(ex["er_ptr"], np.int64)
-    er_col = np.asarray(ex["er_col"], np.int64)
-    er_val = np.asarray(ex["er_val"])
-    for i in range(len(er_row)):
-        for k in range(er_ptr[i], er_ptr[i + 1]):
-            rows.append(n2o[er_row[i]])
-            cols.append(n2o[er_col[k]])
-            vals.append(er_val[k])
+    if int(ex.get("er_layout", 1)) == 0:
+        # extra entries stored in the slab's own slices: same lane -> row map, 32-bit new columns
+        er_pos = np.asarray(ex["er_slice_pos"], np.int64)
+        er_col = np.asarray(ex["er_scol"], np.int64)
+        er_val = np.asarray(ex["er_sval"])
+        ecnt = np.asarray(ex["row_er_count"], np.int64)
+        for p in range(len(part_ptr) - 1):
+            pb, pe = part_ptr[p], part_ptr[p + 1]
+            for s in range(slice_ptr[p], slice_ptr[p + 1]):
+                width = (er_pos[s + 1] - er_pos[s]) // 32
+                for lane in range(32):
+                    row = pb + (s - slice_ptr[p]) * rps + lane // tpr
+                    if row >= pe:
+                        continue
+                    for k in range(width):
+                        j = k * tpr + lane % tpr
+                        if j >= ecnt[row]:
+                            continue
+                        e = er_pos[s] + 32 * k + lane
+                        rows.append(n2o[row])
+                        cols.append(n2o[er_col[e]])
+                        vals.append(er_val[e])
+    else:
+        er_row = np.asarray(ex["er_row"], np.int64)
+        er_ptr = np.asarray(ex["er_ptr"], np.int64)
+        er_col = np.asarray(ex["er_col"], np.int64)
+        er_val = np.asarray(ex["er_val"])
+        for i in range(len(er_row)):
+            for k in range(er_ptr[i], er_ptr[i + 1]):
+                rows.append(n2o[er_row[i]])
+                cols.append(n2o[er_col[k]])
+                vals.append(er_val[k])
     return (np.asarray(rows, np.int64), np.asarray(cols, np.int64), np.asarray(vals, np.float64))
 
 

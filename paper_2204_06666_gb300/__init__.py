@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("er_tpr", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("lowp", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("smem_budget", ctypes.c_int32),
                 ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
-                ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("er_layout", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -52,7 +53,8 @@ class PlanInfo(ctypes.Structure):
                 ("lowp", ctypes.c_int32), ("ell_nnz", ctypes.c_int64), ("ell_stored", ctypes.c_int64),
                 ("er_rows", ctypes.c_int64), ("er_nnz", ctypes.c_int64), ("bytes_effective", ctypes.c_int64),
                 ("bytes_device", ctypes.c_int64), ("partition_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
-                ("upload_ms", ctypes.c_double), ("device_status", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+                ("upload_ms", ctypes.c_double), ("device_status", ctypes.c_int32), ("num_sms", ctypes.c_int32),
+                ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -63,7 +65,9 @@ class PlanExport(ctypes.Structure):
                 ("tpr", ctypes.c_int32), ("ell_stored", ctypes.c_int64), ("er_rows", ctypes.c_int64),
                 ("er_nnz", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in (
                     "new_to_old", "part_ptr", "slice_ptr", "slice_pos", "ell_col", "ell_val", "row_ell_count",
-                    "er_part_ptr", "er_row", "er_ptr", "er_col", "er_val")]
+                    "er_part_ptr", "er_row", "er_ptr", "er_col", "er_val")] + [
+                ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64), ("er_slice_pos", ctypes.c_void_p),
+                ("er_scol", ctypes.c_void_p), ("er_sval", ctypes.c_void_p), ("row_er_count", ctypes.c_void_p)]
 
 
 _P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -277,7 +281,11 @@ class Plan:
                 "row_ell_count": arr(ex.row_ell_count, n, np.int32),
                 "er_part_ptr": arr(ex.er_part_ptr, nparts + 1, np.int32),
                 "er_row": arr(ex.er_row, ex.er_rows, np.int32), "er_ptr": arr(ex.er_ptr, ex.er_rows + 1, np.int64),
-                "er_col": arr(ex.er_col, ex.er_nnz, np.int32), "er_val": arr(ex.er_val, ex.er_nnz, np.float64)}
+                "er_col": arr(ex.er_col, ex.er_nnz, np.int32), "er_val": arr(ex.er_val, ex.er_nnz, np.float64),
+                "er_layout": ex.er_layout, "er_slice_pos": arr(ex.er_slice_pos, ns + 1, np.int64),
+                "er_scol": arr(ex.er_scol, ex.er_stored if ex.er_layout == 0 else 0, np.int32),
+                "er_sval": arr(ex.er_sval, ex.er_stored if ex.er_layout == 0 else 0, np.float64),
+                "row_er_count": arr(ex.row_er_count, n, np.int32)}
 
     def profile_enable(self, on: bool = True):
         _check(_lib.ehyb_profile_enable(self._h, int(on)), "ehyb_profile_enable")

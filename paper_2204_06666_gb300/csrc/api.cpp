@@ -128,7 +128,8 @@ struct ehyb_plan_s {
   double* hy = nullptr;
   int32_t lowp = 0;
   int32_t er_tpr = 1;
-  int64_t ell_nnz = 0, ell_stored = 0, er_rows = 0, er_nnz = 0;
+  int32_t er_layout = 0;
+  int64_t ell_nnz = 0, ell_stored = 0, er_rows = 0, er_nnz = 0, er_stored = 0;
   int32_t nslices = 0, slice_rows = 0, num_sms = 0;
   double upload_ms = 0;
   int device = -1;
@@ -200,8 +201,9 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   if (opt.ell_tpr == 0) opt.ell_tpr = 1;
   if (!is_pow2_in(opt.ell_tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
   if (opt.er_tpr != 0 && !is_pow2_in(opt.er_tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
-  if (opt.block_threads == 0) opt.block_threads = 512;
-  if (opt.block_threads < 32 || opt.block_threads > 1024 || opt.block_threads % 32) return EHYB_ERR_INVALID_ARG;
+  if (opt.block_threads != 0 && (opt.block_threads < 32 || opt.block_threads > 1024 || opt.block_threads % 32))
+    return EHYB_ERR_INVALID_ARG;
+  if (opt.er_layout < 0 || opt.er_layout > 1) return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
       opt.num_sms < 0 || opt.wait_timeout_ns < 0)
     return EHYB_ERR_INVALID_ARG;
@@ -235,6 +237,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   prm.ell_width_cap = opt.ell_width_cap;
   prm.ell_tpr = opt.ell_tpr;
   prm.lowp = opt.lowp;
+  prm.er_layout = opt.er_layout;
   prm.part_vec = opt.part_vec;
   HostPlan& H = P->host;
   try {
@@ -252,8 +255,11 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   P->slice_rows = prm.slice_rows;
   P->ell_nnz = H.ell_nnz;
   P->ell_stored = (int64_t)H.ell_col.size();
-  P->er_rows = (int64_t)H.er_row.size();
-  P->er_nnz = (int64_t)H.er_col.size();
+  P->er_rows = 0;
+  for (int64_t r = 0; r < n; ++r) P->er_rows += H.row_er_count[(size_t)r] > 0;
+  P->er_nnz = H.er_nnz;
+  P->er_stored = H.er_layout == 0 ? (int64_t)H.er_scol.size() : H.er_nnz;
+  P->er_layout = H.er_layout;
   P->nslices = H.nslices;
   if (opt.er_tpr) {
     P->er_tpr = opt.er_tpr;
@@ -266,7 +272,12 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   D.nparts = H.nparts;
   D.tpr = H.tpr;
   D.er_tpr = P->er_tpr;
+  if (opt.block_threads == 0) {  // enough warps for the average partition's slices
+    const int64_t per_part = H.nparts ? ((int64_t)H.nslices + H.nparts - 1) / H.nparts : 1;
+    opt.block_threads = (int32_t)std::min<int64_t>(1024, std::max<int64_t>(128, 32 * per_part));
+  }
   D.threads = opt.block_threads;
+  D.er_layout = H.er_layout;
   D.max_part_rows = H.max_part_rows;
   D.wait_timeout_ns = opt.wait_timeout_ns > 0 ? (uint64_t)opt.wait_timeout_ns : 1000000000ull;
   D.inject_wait_fault = opt.inject_wait_fault;
@@ -291,6 +302,11 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     const size_t o_erv = A.add<double>(H.er_val.size());
     const size_t o_erv32 = A.add<float>(H.er_val_f32.size());
     const size_t o_erv16 = A.add<uint16_t>(H.er_val_bf16.size());
+    const size_t o_esp = A.add<int64_t>(H.er_slice_pos.size());
+    const size_t o_esc = A.add<int32_t>(H.er_scol.size());
+    const size_t o_esv = A.add<double>(H.er_sval.size());
+    const size_t o_esv32 = A.add<float>(H.er_sval_f32.size());
+    const size_t o_esv16 = A.add<uint16_t>(H.er_sval_bf16.size());
     const size_t o_xp = A.add<double>((size_t)n + 2);
     const size_t o_xp32 = A.add<float>((size_t)n + 4);
     const size_t o_st = A.add<int32_t>(4);
@@ -308,7 +324,8 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     UP(o_n2o, H.new_to_old) UP(o_pp, H.part_ptr) UP(o_sp, H.slice_ptr) UP(o_pos, H.slice_pos) UP(o_ec, H.ell_col)
     UP(o_ev, H.ell_val) UP(o_ev32, H.ell_val_f32) UP(o_ev16, H.ell_val_bf16) UP(o_epp, H.er_part_ptr)
     UP(o_er, H.er_row) UP(o_erp, H.er_ptr) UP(o_erc, H.er_col) UP(o_erv, H.er_val) UP(o_erv32, H.er_val_f32)
-    UP(o_erv16, H.er_val_bf16)
+    UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_esc, H.er_scol) UP(o_esv, H.er_sval)
+    UP(o_esv32, H.er_sval_f32) UP(o_esv16, H.er_sval_bf16)
 #undef UP
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_st, 0, 16, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_xp, 0, ((size_t)n + 2) * 8, s);
@@ -333,6 +350,11 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     D.er_val = (const double*)(base + o_erv);
     D.er_val_f32 = (const float*)(base + o_erv32);
     D.er_val_bf16 = (const uint16_t*)(base + o_erv16);
+    D.er_slice_pos = (const int64_t*)(base + o_esp);
+    D.er_scol = (const int32_t*)(base + o_esc);
+    D.er_sval = (const double*)(base + o_esv);
+    D.er_sval_f32 = (const float*)(base + o_esv32);
+    D.er_sval_bf16 = (const uint16_t*)(base + o_esv16);
     D.status = (int32_t*)(base + o_st);
     P->xp = (double*)(base + o_xp);
     P->xp32 = (float*)(base + o_xp32);
@@ -349,6 +371,10 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     std::vector<double>().swap(h.er_val);
     std::vector<float>().swap(h.er_val_f32);
     std::vector<uint16_t>().swap(h.er_val_bf16);
+    std::vector<int32_t>().swap(h.er_scol);
+    std::vector<double>().swap(h.er_sval);
+    std::vector<float>().swap(h.er_sval_f32);
+    std::vector<uint16_t>().swap(h.er_sval_bf16);
     std::vector<int32_t>().swap(h.old_to_new);
   }
   *out = P.release();
@@ -492,7 +518,10 @@ ehyb_status_t ehyb_plan_info(ehyb_plan_t p, ehyb_plan_info_t* info) {
   info->ell_stored = p->ell_stored;
   info->er_rows = p->er_rows;
   info->er_nnz = p->er_nnz;
-  info->bytes_effective = p->ell_nnz * 10 + p->er_nnz * 12 + p->er_rows * 8 + H.n * 16;
+  // values + column indices + x + y; the CSR layout also reads yIdxER and a line offset per ER line
+  info->bytes_effective = p->ell_nnz * 10 + p->er_nnz * 12 + (p->er_layout == 1 ? p->er_rows * 8 : 0) + H.n * 16;
+  info->er_layout = p->er_layout;
+  info->er_stored = p->er_stored;
   info->bytes_device = (int64_t)p->arena_bytes;
   info->partition_ms = H.partition_ms;
   info->reorder_ms = H.reorder_ms;
@@ -512,19 +541,30 @@ ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
   HostPlan& H = p->host;
   if (!p->host_kept && !p->exported) {  // copy the bulky arrays back from the device
     CK(cudaDeviceSynchronize());
+    const bool sl = p->er_layout == 0;
     try {
       H.ell_col.resize((size_t)p->ell_stored);
       H.ell_val.resize((size_t)p->ell_stored);
-      H.er_col.resize((size_t)p->er_nnz);
-      H.er_val.resize((size_t)p->er_nnz);
+      H.er_col.resize(sl ? 0 : (size_t)p->er_nnz);
+      H.er_val.resize(sl ? 0 : (size_t)p->er_nnz);
+      H.er_scol.resize(sl ? (size_t)p->er_stored : 0);
+      H.er_sval.resize(sl ? (size_t)p->er_stored : 0);
     } catch (const std::bad_alloc&) {
       return EHYB_ERR_OOM;
     }
     const DevPlan& D = p->dev;
-    CK(cudaMemcpy(H.ell_col.data(), D.ell_col, H.ell_col.size() * 2, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(H.ell_val.data(), D.ell_val, H.ell_val.size() * 8, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(H.er_col.data(), D.er_col, H.er_col.size() * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(H.er_val.data(), D.er_val, H.er_val.size() * 8, cudaMemcpyDeviceToHost));
+    if (!H.ell_col.empty()) {
+      CK(cudaMemcpy(H.ell_col.data(), D.ell_col, H.ell_col.size() * 2, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(H.ell_val.data(), D.ell_val, H.ell_val.size() * 8, cudaMemcpyDeviceToHost));
+    }
+    if (!H.er_col.empty()) {
+      CK(cudaMemcpy(H.er_col.data(), D.er_col, H.er_col.size() * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(H.er_val.data(), D.er_val, H.er_val.size() * 8, cudaMemcpyDeviceToHost));
+    }
+    if (!H.er_scol.empty()) {
+      CK(cudaMemcpy(H.er_scol.data(), D.er_scol, H.er_scol.size() * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(H.er_sval.data(), D.er_sval, H.er_sval.size() * 8, cudaMemcpyDeviceToHost));
+    }
     p->exported = true;
   }
   ex->n = H.n;
@@ -532,8 +572,8 @@ ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
   ex->nslices = H.nslices;
   ex->tpr = H.tpr;
   ex->ell_stored = p->ell_stored;
-  ex->er_rows = p->er_rows;
-  ex->er_nnz = p->er_nnz;
+  ex->er_rows = (int64_t)H.er_row.size();
+  ex->er_nnz = p->er_layout == 1 ? p->er_nnz : 0;
   ex->new_to_old = H.new_to_old.data();
   ex->part_ptr = H.part_ptr.data();
   ex->slice_ptr = H.slice_ptr.data();
@@ -546,6 +586,12 @@ ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
   ex->er_ptr = H.er_ptr.data();
   ex->er_col = H.er_col.data();
   ex->er_val = H.er_val.data();
+  ex->er_layout = p->er_layout;
+  ex->er_stored = p->er_stored;
+  ex->er_slice_pos = H.er_slice_pos.data();
+  ex->er_scol = H.er_scol.data();
+  ex->er_sval = H.er_sval.data();
+  ex->row_er_count = H.row_er_count.data();
   return EHYB_OK;
 }
 

@@ -26,6 +26,12 @@ struct DevPlan {
   const double* er_val = nullptr;
   const float* er_val_f32 = nullptr;
   const uint16_t* er_val_bf16 = nullptr;
+  int32_t er_layout = 0;  // 0: sliced with the slab slices; 1: CSR lines
+  const int64_t* er_slice_pos = nullptr;
+  const int32_t* er_scol = nullptr;
+  const double* er_sval = nullptr;
+  const float* er_sval_f32 = nullptr;
+  const uint16_t* er_sval_bf16 = nullptr;
   int32_t* status = nullptr;  // device status word (first fault wins)
   uint64_t wait_timeout_ns = 1000000000ull;
   int32_t inject_wait_fault = 0;

@@ -251,7 +251,12 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   P.max_part_rows = 0;
   for (int32_t p = 0; p < nparts; ++p) {
     auto b = P.new_to_old.begin() + P.part_ptr[(size_t)p], e = P.new_to_old.begin() + P.part_ptr[(size_t)p + 1];
-    std::stable_sort(b, e, [&](int32_t a, int32_t c) { return cin[(size_t)a] > cin[(size_t)c]; });
+    // Alg. 1 sorts by in-partition count, descending; ties go to the larger extra-row count first,
+    // which keeps the extra-row widths of a 32-row slice close together (less slice padding)
+    std::stable_sort(b, e, [&](int32_t a, int32_t c) {
+      if (cin[(size_t)a] != cin[(size_t)c]) return cin[(size_t)a] > cin[(size_t)c];
+      return cer[(size_t)a] > cer[(size_t)c];
+    });
     P.max_part_rows = std::max(P.max_part_rows, P.part_ptr[(size_t)p + 1] - P.part_ptr[(size_t)p]);
   }
   if (P.max_part_rows > 65536) return 4;  // the 16-bit column offset would overflow
@@ -279,10 +284,33 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   }
   const int64_t stored = P.slice_pos[(size_t)P.nslices];
 
-  // ER lines: rows with extra entries, per partition, sorted by ER count descending (stable)
+  P.er_layout = prm.er_layout;
+  P.row_er_count.resize((size_t)n);
+  for (int64_t r = 0; r < n; ++r) P.row_er_count[(size_t)r] = cer[(size_t)P.new_to_old[(size_t)r]];
+  P.er_nnz = 0;
+  for (int64_t i = 0; i < n; ++i) P.er_nnz += cer[(size_t)i];
+
+  // er_layout 0: ER entries in the slab's own 32-lane slices (same lane -> row map, column-major)
+  P.er_slice_pos.assign((size_t)P.nslices + 1, 0);
+  if (P.er_layout == 0) {
+    for (int32_t p = 0; p < nparts; ++p) {
+      const int32_t pb = P.part_ptr[(size_t)p], pe = P.part_ptr[(size_t)p + 1];
+      for (int32_t s = P.slice_ptr[(size_t)p]; s < P.slice_ptr[(size_t)p + 1]; ++s) {
+        int32_t r0 = pb + (s - P.slice_ptr[(size_t)p]) * rps;
+        int32_t r1 = std::min(pe, r0 + rps);
+        int32_t w = 0;
+        for (int32_t r = r0; r < r1; ++r) w = std::max(w, P.row_er_count[(size_t)r]);
+        w = (w + tpr - 1) / tpr;
+        P.er_slice_pos[(size_t)s + 1] = P.er_slice_pos[(size_t)s] + 32 * (int64_t)w;
+      }
+    }
+  }
+  const int64_t er_stored = P.er_slice_pos[(size_t)P.nslices];
+
+  // er_layout 1: ER lines (rows with extra entries), per partition, sorted by ER count descending
   P.er_part_ptr.assign((size_t)nparts + 1, 0);
   P.er_row.clear();
-  for (int32_t p = 0; p < nparts; ++p) {
+  for (int32_t p = 0; p < nparts && P.er_layout == 1; ++p) {
     size_t b = P.er_row.size();
     for (int32_t r = P.part_ptr[(size_t)p]; r < P.part_ptr[(size_t)p + 1]; ++r)
       if (cer[(size_t)P.new_to_old[(size_t)r]] > 0) P.er_row.push_back(r);
@@ -306,6 +334,13 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   P.ell_val.assign((size_t)stored, 0.0);
   P.er_col.assign((size_t)er_nnz, 0);
   P.er_val.assign((size_t)er_nnz, 0.0);
+  P.er_scol.assign((size_t)er_stored, 0);
+  P.er_sval.assign((size_t)er_stored, 0.0);
+  // padding slots of the sliced ER part point at the first row of their partition (value 0)
+  for (int32_t p = 0; p < nparts && P.er_layout == 0; ++p)
+    for (int64_t k = P.er_slice_pos[(size_t)P.slice_ptr[(size_t)p]];
+         k < P.er_slice_pos[(size_t)P.slice_ptr[(size_t)p + 1]]; ++k)
+      P.er_scol[(size_t)k] = P.part_ptr[(size_t)p];
   P.row_ell_count.resize((size_t)n);
   P.ell_nnz = 0;
   std::vector<int32_t> part_of_new((size_t)nparts > 0 ? (size_t)n : 0);
@@ -316,9 +351,11 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     const int32_t p = part_of_new[(size_t)r];
     const int32_t pb = P.part_ptr[(size_t)p];
     const int32_t l = (int32_t)r - pb;
-    const int64_t base = P.slice_pos[(size_t)(P.slice_ptr[(size_t)p] + l / rps)];
+    const int32_t sl = P.slice_ptr[(size_t)p] + l / rps;
+    const int64_t base = P.slice_pos[(size_t)sl];
+    const int64_t ebase = P.er_slice_pos[(size_t)sl];
     const int32_t lane0 = (l % rps) * tpr;
-    int64_t j = 0;
+    int64_t j = 0, je = 0;
     int64_t eo = line_of[(size_t)r] >= 0 ? P.er_ptr[(size_t)line_of[(size_t)r]] : -1;
     for (int64_t k = rp[i]; k < rp[(int64_t)i + 1]; ++k) {
       const int32_t c = col[k];
@@ -327,6 +364,11 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
         P.ell_col[(size_t)pos] = (uint16_t)(P.old_to_new[(size_t)c] - pb);
         P.ell_val[(size_t)pos] = val[k];
         ++j;
+      } else if (P.er_layout == 0) {
+        const int64_t pos = ebase + 32 * (je / tpr) + lane0 + (int32_t)(je % tpr);
+        P.er_scol[(size_t)pos] = P.old_to_new[(size_t)c];
+        P.er_sval[(size_t)pos] = val[k];
+        ++je;
       } else {
         P.er_col[(size_t)eo] = P.old_to_new[(size_t)c];
         P.er_val[(size_t)eo] = val[k];
@@ -339,13 +381,18 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   if (prm.lowp == 1) {
     P.ell_val_f32.resize((size_t)stored);
     P.er_val_f32.resize((size_t)er_nnz);
+    P.er_sval_f32.resize((size_t)er_stored);
     for (int64_t k = 0; k < stored; ++k) P.ell_val_f32[(size_t)k] = (float)P.ell_val[(size_t)k];
     for (int64_t k = 0; k < er_nnz; ++k) P.er_val_f32[(size_t)k] = (float)P.er_val[(size_t)k];
+    for (int64_t k = 0; k < er_stored; ++k) P.er_sval_f32[(size_t)k] = (float)P.er_sval[(size_t)k];
   } else if (prm.lowp == 2) {
     P.ell_val_bf16.resize((size_t)stored);
     P.er_val_bf16.resize((size_t)er_nnz);
+    P.er_sval_bf16.resize((size_t)er_stored);
     for (int64_t k = 0; k < stored; ++k) P.ell_val_bf16[(size_t)k] = f32_to_bf16_rne((float)P.ell_val[(size_t)k]);
     for (int64_t k = 0; k < er_nnz; ++k) P.er_val_bf16[(size_t)k] = f32_to_bf16_rne((float)P.er_val[(size_t)k]);
+    for (int64_t k = 0; k < er_stored; ++k)
+      P.er_sval_bf16[(size_t)k] = f32_to_bf16_rne((float)P.er_sval[(size_t)k]);
   }
   P.reorder_ms = now_ms() - t1;
   return 0;

@@ -12,6 +12,7 @@ struct PlanParams {
   int32_t ell_width_cap = 0;  // 0 = unlimited
   int32_t ell_tpr = 1;        // lanes per row in a slab slice
   int32_t lowp = 0;           // 0 none, 1 fp32, 2 bf16 value copies
+  int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR
   const int32_t* part_vec = nullptr;
 };
 
@@ -32,6 +33,16 @@ struct HostPlan {
   std::vector<double> er_val;
   std::vector<float> er_val_f32;
   std::vector<uint16_t> er_val_bf16;
+  // er_layout 0: the ER entries of slab slice s, column-major like the slab, 32-bit new-numbering
+  // columns; slice width = (er_slice_pos[s+1] - er_slice_pos[s]) / 32
+  int32_t er_layout = 0;
+  std::vector<int64_t> er_slice_pos;
+  std::vector<int32_t> er_scol;
+  std::vector<double> er_sval;
+  std::vector<float> er_sval_f32;
+  std::vector<uint16_t> er_sval_bf16;
+  std::vector<int32_t> row_er_count;
+  int64_t er_nnz = 0;
   int64_t ell_nnz = 0;
   int32_t max_part_rows = 0;
   double partition_ms = 0, reorder_ms = 0;

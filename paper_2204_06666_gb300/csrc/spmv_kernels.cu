@@ -9,12 +9,17 @@
 //        EHYB_ERR_TIMEOUT in the plan status word and returns);
 //     3. each warp takes 32-lane slices of the partition from a shared counter (the dynamic
 //        slice balancing of Alg. 3) and runs y[row] = sum_k ValELL * CachedVec[ColELL] with the
-//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot;
-//     4. after a block barrier the same block adds the ER lines of its own rows
-//        (extra entries, global gathers of x, er_tpr lanes per line + shuffle reduction),
-//        y[yIdxER] += sum, so that the result is ell_sum + er_sum for every row, deterministic.
-//   The paper's second pass over ER slices from a global counter is folded into step 4: the
-//   rows a block updates are its own, so no atomics and no second launch are needed.
+//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot, eight slots of
+//        values and columns loaded ahead of their FMAs to keep enough bytes in flight;
+//     4. extra-row (ER) entries, two layouts:
+//        - sliced (er_layout 0, default): the ER entries of the slice's own rows are stored in
+//          the same lane -> row arrangement right behind it (the paper stores its ER part as
+//          stride-32 slices too, Alg. 2); the warp continues with them, gathering x from global
+//          memory, and writes y once -- no block barrier, no read-modify-write, no FP64 shuffle;
+//        - CSR lines (er_layout 1): after a block barrier, er_tpr lanes per ER line with a
+//          shuffle reduction, y[yIdxER] += sum.
+//   In both layouts the rows a block updates are its own, so the paper's second pass over ER
+//   slices from a global counter is not needed: no atomics on y, deterministic results.
 //
 // csr_kernel: the plain vector-CSR baseline (Bell & Garland, Sec. 2.2), tpr lanes per row.
 #include "device.h"
@@ -101,8 +106,57 @@ __device__ __forceinline__ float load_val<uint16_t, float>(const uint16_t* p) {
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
+constexpr int kBatch = 8;  // slots whose loads are issued before their FMAs
+
+// acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory
+template <typename V, typename X>
+__device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
+                                      const X* xs, X acc) {
+  int k = 0;
+  for (; k + kBatch <= w; k += kBatch) {
+    X v[kBatch];
+    int c[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
+      c[u] = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u)));
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) acc = fma_t(v[u], xs[c[u]], acc);
+  }
+  for (; k < w; ++k)
+    acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k),
+                xs[__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)k))], acc);
+  return acc;
+}
+
+// acc += sum_{k<w} v[32k] * xg[c[32k]]: sliced extra-row slots of one lane, x from global memory
+template <typename V, typename X>
+__device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __restrict__ cp, int w,
+                                    const X* __restrict__ xg, X acc) {
+  int k = 0;
+  for (; k + kBatch <= w; k += kBatch) {
+    X v[kBatch];
+    int c[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
+      c[u] = __ldcs(cp + 32 * (int64_t)(k + u));
+    }
+    X xv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) xv[u] = __ldg(xg + c[u]);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) acc = fma_t(v[u], xv[u], acc);
+  }
+  for (; k < w; ++k) acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k), __ldg(xg + __ldcs(cp + 32 * (int64_t)k)), acc);
+  return acc;
+}
+
 struct KArgs {
   int32_t tpr_log2, er_tpr_log2;
+  const int64_t* er_slice_pos;
+  const int32_t* er_scol;
   const int32_t* new_to_old;
   const int32_t* part_ptr;
   const int32_t* slice_ptr;
@@ -118,7 +172,7 @@ struct KArgs {
 };
 
 // V: stored value type; X: type of x, y and of the accumulation
-template <typename V, typename X, bool SCATTER>
+template <typename V, typename X, bool SCATTER, bool ER_SLICED>
 __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
                                                     const V* __restrict__ er_val, const X* __restrict__ xp,
                                                     X* __restrict__ y) {
@@ -184,14 +238,11 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
   while (s < s1) {
     const int64_t pos = a.slice_pos[s];
     const int w = (int)((a.slice_pos[s + 1] - pos) >> 5);
-    const V* vp = ell_val + pos + lane;
-    const uint16_t* cp = a.ell_col + pos + lane;
-    X acc = X(0);
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-      const X v = load_val<V, X>(vp + 32 * (int64_t)k);
-      const int c = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)k));
-      acc = fma_t(v, xsl[c], acc);
+    X acc = slab_dot<V, X>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
+    if (ER_SLICED) {
+      const int64_t epos = a.er_slice_pos[s];
+      const int we = (int)((a.er_slice_pos[s + 1] - epos) >> 5);
+      acc = er_dot<V, X>(er_val + epos + lane, a.er_scol + epos + lane, we, xp, acc);
     }
     for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
@@ -203,6 +254,7 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     if (lane == 0) nxt = atomicAdd(&slice_counter, 1);
     s = __shfl_sync(FULL, nxt, 0);
   }
+  if (ER_SLICED) return;
   const int e0 = a.er_part_ptr[p];
   const int e1 = a.er_part_ptr[p + 1];
   if (e0 == e1) return;
@@ -217,8 +269,21 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     X acc = X(0);
     if (e < e1) {
       const int64_t k1 = a.er_ptr[e + 1];
-      for (int64_t k = a.er_ptr[e] + esub; k < k1; k += etpr)
-        acc = fma_t(load_val<V, X>(er_val + k), __ldg(xp + __ldcs(a.er_col + k)), acc);
+      int64_t k = a.er_ptr[e] + esub;
+      for (; k + 3 * etpr < k1; k += 4 * etpr) {  // four entries' loads in flight
+        X v[4], xv[4];
+        int c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = load_val<V, X>(er_val + k + u * etpr);
+          c[u] = __ldcs(a.er_col + k + u * etpr);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = __ldg(xp + c[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fma_t(v[u], xv[u], acc);
+      }
+      for (; k < k1; k += etpr) acc = fma_t(load_val<V, X>(er_val + k), __ldg(xp + __ldcs(a.er_col + k)), acc);
     }
     for (int off = etpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     if (esub == 0 && e < e1) {
@@ -265,6 +330,8 @@ KArgs make_args(const DevPlan& P) {
   KArgs a;
   a.tpr_log2 = ilog2(P.tpr);
   a.er_tpr_log2 = ilog2(P.er_tpr);
+  a.er_slice_pos = P.er_slice_pos;
+  a.er_scol = P.er_scol;
   a.new_to_old = P.new_to_old;
   a.part_ptr = P.part_ptr;
   a.slice_ptr = P.slice_ptr;
@@ -294,20 +361,23 @@ size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes) {
   return (b + 15) & ~(size_t)15;
 }
 
+template <typename V, typename X>
+static cudaError_t set_smem(int bytes) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+    return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+    return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+    return e;
+  return cudaFuncSetAttribute(ehyb_kernel<V, X, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 cudaError_t kernels_init(int smem_optin) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(ehyb_kernel<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ehyb_kernel<double, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ehyb_kernel<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ehyb_kernel<float, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ehyb_kernel<uint16_t, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(ehyb_kernel<uint16_t, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_optin);
+  if ((e = set_smem<double, double>(smem_optin))) return e;
+  if ((e = set_smem<float, float>(smem_optin))) return e;
+  return set_smem<uint16_t, float>(smem_optin);
 }
 
 cudaError_t launch_permute_f64(const DevPlan& P, int to_new, const double* in, double* out, cudaStream_t s) {
@@ -322,28 +392,34 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
   return cudaGetLastError();
 }
 
+template <typename V, typename X>
+static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const V* erv_sl, const X* xp, X* y,
+                         int scatter, size_t smem, cudaStream_t s) {
+  KArgs a = make_args(P);
+  const bool sl = P.er_layout == 0;
+  const V* erv = sl ? erv_sl : erv_csr;
+  if (scatter) {
+    if (sl) ehyb_kernel<V, X, true, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    else ehyb_kernel<V, X, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+  } else {
+    if (sl) ehyb_kernel<V, X, false, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    else ehyb_kernel<V, X, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+  }
+}
+
 cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s) {
   if (P.nparts == 0) return cudaSuccess;
-  const size_t smem = ehyb_smem_bytes(P, 8);
-  KArgs a = make_args(P);
-  if (scatter) ehyb_kernel<double, double, true><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val, P.er_val, xp, y);
-  else ehyb_kernel<double, double, false><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val, P.er_val, xp, y);
+  launch_typed<double, double>(P, P.ell_val, P.er_val, P.er_sval, xp, y, scatter, ehyb_smem_bytes(P, 8), s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s) {
   if (P.nparts == 0) return cudaSuccess;
   const size_t smem = ehyb_smem_bytes(P, 4);
-  KArgs a = make_args(P);
-  if (lowp == 1) {
-    if (scatter) ehyb_kernel<float, float, true><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_f32, P.er_val_f32, xp, y);
-    else ehyb_kernel<float, float, false><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_f32, P.er_val_f32, xp, y);
-  } else {
-    if (scatter)
-      ehyb_kernel<uint16_t, float, true><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_bf16, P.er_val_bf16, xp, y);
-    else
-      ehyb_kernel<uint16_t, float, false><<<P.nparts, P.threads, smem, s>>>(a, P.ell_val_bf16, P.er_val_bf16, xp, y);
-  }
+  if (lowp == 1)
+    launch_typed<float, float>(P, P.ell_val_f32, P.er_val_f32, P.er_sval_f32, xp, y, scatter, smem, s);
+  else
+    launch_typed<uint16_t, float>(P, P.ell_val_bf16, P.er_val_bf16, P.er_sval_bf16, xp, y, scatter, smem, s);
   return cudaGetLastError();
 }
 

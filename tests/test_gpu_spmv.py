@@ -45,9 +45,12 @@ def _check_fp(A, x, y):
     return err
 
 
-OPTS = [dict(), dict(ell_tpr=2, er_tpr=1), dict(ell_tpr=4, er_tpr=32), dict(ell_tpr=32, er_tpr=8),
-        dict(ell_width_cap=6, er_tpr=4), dict(slice_rows=37, block_threads=64), dict(slice_rows=1),
-        dict(slice_rows=2000, block_threads=1024), dict(slice_rows=33, block_threads=32)]
+OPTS = [dict(), dict(ell_tpr=2), dict(ell_tpr=4), dict(ell_tpr=32), dict(ell_width_cap=6),
+        dict(slice_rows=37, block_threads=64), dict(slice_rows=1), dict(slice_rows=2000, block_threads=1024),
+        dict(slice_rows=33, block_threads=32),
+        dict(er_layout=1, ell_tpr=2, er_tpr=1), dict(er_layout=1, ell_tpr=4, er_tpr=32),
+        dict(er_layout=1, ell_tpr=32, er_tpr=8), dict(er_layout=1, ell_width_cap=6, er_tpr=4),
+        dict(er_layout=1, slice_rows=37, block_threads=64)]
 
 
 @pytest.mark.parametrize("opt", OPTS)
@@ -60,12 +63,13 @@ def test_integer_bit_exact_ragged(eh, opt, seed):
     assert np.array_equal(y, oracle.spmv(A, x))
 
 
+@pytest.mark.parametrize("er_layout", [0, 1])
 @pytest.mark.parametrize("name,N,slice_rows", [("fem2d", 200, 0), ("hex", 16, 0), ("hex", 16, 700),
                                                ("tet", 20, 0), ("tet", 20, 1000)])
-def test_fem_parity(eh, name, N, slice_rows):
+def test_fem_parity(eh, name, N, slice_rows, er_layout):
     A = {"fem2d": gen.fem2d_p1, "hex": gen.hex_elast3d, "tet": gen.tet_lap3d}[name](N=N)
     x = gen.uniform(A.n, 13)
-    _, y = _run(eh, A, x, slice_rows=slice_rows)
+    _, y = _run(eh, A, x, slice_rows=slice_rows, er_layout=er_layout)
     _check_fp(A, x, y)
 
 

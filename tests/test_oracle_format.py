@@ -31,13 +31,28 @@ def test_decode_hand_derived_example():
     assert ef.same_multiset(ef.decode(p), ef.triplets(A))
 
 
+def test_decode_hand_derived_example_sliced_extra_rows():
+    g, p, A = golden_plan()
+    q = {k: v for k, v in p.items() if not k.startswith("er_")}
+    q["er_layout"] = 0
+    q["er_slice_pos"] = p["er_slice_pos"]
+    size = p["er_slice_pos"][-1]
+    q["er_scol"] = np.full(size, p["er_slice_pad_col"][0], np.int32)
+    q["er_sval"] = np.zeros(size)
+    for pos, c, v in p["er_slice_entries"]:
+        q["er_scol"][pos], q["er_sval"][pos] = c, v
+    assert ef.same_multiset(ef.decode(q), ef.triplets(A))
+    q["row_er_count"] = [0, 1, 0, 0, 0]   # the extra entry attributed to the wrong row is dropped
+    assert not ef.same_multiset(ef.decode(q), ef.triplets(A))
+
+
 def test_decode_detects_a_misplaced_entry():
     g, p, A = golden_plan()
     p["ell_col"] = p["ell_col"].copy()
     p["ell_col"][96] = 1          # wrong local column for entry (1,2)
     assert not ef.same_multiset(ef.decode(p), ef.triplets(A))
     g, p, A = golden_plan()
-    p["new_to_old"] = [0, 3, 4, 1, 2]   # rows swapped
+    p["new_to_old"] = [3, 0, 4, 1, 2]   # rows swapped
     assert not ef.same_multiset(ef.decode(p), ef.triplets(A))
 
 

@@ -19,15 +19,29 @@ def _plan(A, **kw):
 def test_golden_plan_matches_hand_derivation_exactly():
     g = json.load(open(GOLDEN))
     A = gen.CSR(g["n"], np.array(g["row_ptr"], np.int64), np.array(g["col"], np.int32), np.array(g["val"], float))
-    ex = _plan(A, part_vec=g["part_vec"]).export()
-    for k in ("new_to_old", "part_ptr", "slice_ptr", "slice_pos", "row_ell_count", "er_row", "er_ptr", "er_col"):
-        assert list(ex[k]) == g["plan"][k], k
-    assert list(ex["er_val"]) == g["plan"]["er_val"]
     want_col = np.zeros(g["plan"]["slice_pos"][-1], np.uint16)
     want_val = np.zeros(g["plan"]["slice_pos"][-1])
     for pos, c, v in g["plan"]["ell_entries"]:
         want_col[pos], want_val[pos] = c, v
+    # extra rows as CSR lines
+    ex = _plan(A, part_vec=g["part_vec"], er_layout=1).export()
+    for k in ("new_to_old", "part_ptr", "slice_ptr", "slice_pos", "row_ell_count", "er_row", "er_ptr", "er_col",
+              "row_er_count"):
+        assert list(ex[k]) == g["plan"][k], k
+    assert list(ex["er_val"]) == g["plan"]["er_val"]
     assert np.array_equal(ex["ell_col"], want_col) and np.array_equal(ex["ell_val"], want_val)
+    # extra rows sliced with the slab
+    ex = _plan(A, part_vec=g["part_vec"]).export()
+    assert ex["er_layout"] == 0 and ex["er_row"].size == 0
+    assert list(ex["new_to_old"]) == g["plan"]["new_to_old"]
+    assert np.array_equal(ex["ell_col"], want_col) and np.array_equal(ex["ell_val"], want_val)
+    assert list(ex["er_slice_pos"]) == g["plan"]["er_slice_pos"]
+    size = g["plan"]["er_slice_pos"][-1]
+    scol = np.full(size, g["plan"]["er_slice_pad_col"][0], np.int32)
+    sval = np.zeros(size)
+    for pos, c, v in g["plan"]["er_slice_entries"]:
+        scol[pos], sval[pos] = c, v
+    assert np.array_equal(ex["er_scol"], scol) and np.array_equal(ex["er_sval"], sval)
 
 
 def _invariants(A, ex, cap=None, width_cap=0):
@@ -43,15 +57,21 @@ def _invariants(A, ex, cap=None, width_cap=0):
     if cap:
         assert sizes.max(initial=0) <= cap
     cnt = ex["row_ell_count"]
-    er_cnt = np.zeros(n, np.int64)
-    er_cnt[ex["er_row"]] = np.diff(ex["er_ptr"])
+    er_cnt = ex["row_er_count"].astype(np.int64)
+    if ex["er_layout"] == 1:
+        line_cnt = np.zeros(n, np.int64)
+        line_cnt[ex["er_row"]] = np.diff(ex["er_ptr"])
+        assert np.array_equal(line_cnt, er_cnt)
     for p in range(len(pp) - 1):
         c = cnt[pp[p]:pp[p + 1]]
         assert np.all(np.diff(c) <= 0)                                   # Alg. 1: descending within a partition
-        e0, e1 = ex["er_part_ptr"][p], ex["er_part_ptr"][p + 1]
-        rows = ex["er_row"][e0:e1]
-        assert np.all((rows >= pp[p]) & (rows < pp[p + 1]))              # ER lines owned by their partition
-        assert np.all(np.diff(er_cnt[rows]) <= 0)                        # ER lines by count, descending
+        tie = np.diff(c) == 0
+        assert np.all(np.diff(er_cnt[pp[p]:pp[p + 1]])[tie] <= 0)        # ties: more extra entries first
+        if ex["er_layout"] == 1:
+            e0, e1 = ex["er_part_ptr"][p], ex["er_part_ptr"][p + 1]
+            rows = ex["er_row"][e0:e1]
+            assert np.all((rows >= pp[p]) & (rows < pp[p + 1]))          # ER lines owned by their partition
+            assert np.all(np.diff(er_cnt[rows]) <= 0)                    # ER lines by count, descending
         ns = ex["slice_ptr"][p + 1] - ex["slice_ptr"][p]
         assert ns == -(-(pp[p + 1] - pp[p]) // (32 // ex["tpr"]))         # slices never straddle partitions
     assert np.all(ex["ell_col"].astype(np.int64) < np.maximum(1, sizes.max(initial=1)))
@@ -59,11 +79,16 @@ def _invariants(A, ex, cap=None, width_cap=0):
         assert cnt.max(initial=0) <= width_cap
     assert np.array_equal(np.sort(np.unique(ex["er_row"])), np.sort(ex["er_row"]))  # one line per row
     assert np.all(np.diff(ex["slice_pos"]) % 32 == 0)
+    if ex["er_layout"] == 0:
+        assert np.all(np.diff(ex["er_slice_pos"]) % 32 == 0)
+        assert ex["er_scol"].size == ex["er_slice_pos"][-1]
+        assert np.all((ex["er_scol"] >= 0) & (ex["er_scol"] < max(n, 1)))  # padding points inside the matrix
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(ell_tpr=2), dict(ell_tpr=4, er_tpr=8), dict(ell_tpr=32),
                                 dict(ell_width_cap=5), dict(slice_rows=37), dict(slice_rows=1),
-                                dict(lowp=1), dict(lowp=2)])
+                                dict(lowp=1), dict(lowp=2), dict(er_layout=1), dict(er_layout=1, ell_tpr=4),
+                                dict(er_layout=1, ell_width_cap=3, slice_rows=50)])
 def test_decode_multiset_random_ragged(kw):
     A = gen.random_csr(700, 7, mean_row=9, empty_frac=0.1, long_rows=3, long_len=400, duplicates=True)
     ex = _plan(A, **kw).export()
@@ -71,11 +96,12 @@ def test_decode_multiset_random_ragged(kw):
     _invariants(A, ex, cap=kw.get("slice_rows"), width_cap=kw.get("ell_width_cap", 0))
 
 
+@pytest.mark.parametrize("er_layout", [0, 1])
 @pytest.mark.parametrize("name", ["fem2d", "hex", "tet"])
-def test_decode_multiset_fem(name):
+def test_decode_multiset_fem(name, er_layout):
     A = {"fem2d": lambda: gen.fem2d_p1(N=40), "hex": lambda: gen.hex_elast3d(N=8),
          "tet": lambda: gen.tet_lap3d(N=12)}[name]()
-    P = _plan(A, slice_rows=200)
+    P = _plan(A, slice_rows=200, er_layout=er_layout)
     ex = P.export()
     assert ef.same_multiset(ef.decode(ex), ef.triplets(A))
     _invariants(A, ex, cap=200)
@@ -112,6 +138,14 @@ def test_partition_quality_3d_hex():
 
 def test_footprint_model_matches_sec_3_4():
     A = gen.fem2d_p1(N=50)
-    info = _plan(A).info()
     n = A.n
+    info = _plan(A).info()
+    assert info["bytes_effective"] == 10 * info["ell_nnz"] + 12 * info["er_nnz"] + 16 * n
+    info = _plan(A, er_layout=1).info()
     assert info["bytes_effective"] == 10 * info["ell_nnz"] + 12 * info["er_nnz"] + 8 * info["er_rows"] + 16 * n
+
+
+def test_sliced_extra_rows_padding_is_small_on_hex():
+    A = gen.hex_elast3d(N=30)
+    info = _plan(A, slice_rows=6770).info()
+    assert info["er_stored"] <= 1.15 * info["er_nnz"]
