@@ -45,6 +45,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 WORKLOADS = {
     "hex_elast3d_70": dict(kind="hex", N=70, seed_x=13,
                            desc="3D Q1 hex elasticity, 70^3 nodes x 3 dof, jitter 0.2h, node relabelling"),
+    "hex_elast3d_48": dict(kind="hex", N=48, seed_x=13,
+                           desc="3D Q1 hex elasticity, 48^3 nodes x 3 dof (profiling size, 0.27 GB slab)"),
     "fem2d_p1_200": dict(kind="fem2d", N=200, seed_x=3, desc="2D P1 Laplacian, 200^2 nodes, jitter 0.3h"),
     "tet_lap3d_126": dict(kind="tet", N=126, seed_x=23, desc="3D P1 tet Laplacian, 126^3 nodes, Dirichlet"),
 }
