@@ -181,6 +181,38 @@ ehyb_status_t ehyb_spmv_noalloc(ehyb_plan_t plan, const double* x, double* y, vo
  * device arrays in the original numbering.  EHYB_ERR_UNSUPPORTED if the plan has no lowp copy. */
 ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t plan, const float* x, float* y, void* stream);
 
+/* ---- conjugate gradients on a plan (Sec. 6: SpMV-dominated iterative solvers) ---- */
+
+typedef struct {
+  int32_t iterations;        /* CG iterations (refinement: inner iterations summed over the outer steps) */
+  int32_t refinements;       /* outer FP64 residual corrections (refine != 0) */
+  int32_t converged;         /* 1 when the stopping test was met */
+  int32_t pad;
+  double relres;             /* ||b - A x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
+  double relres_recursive;   /* FP64 CG: sqrt(r.r)/||b|| of the recursion at exit; refinement: last outer residual */
+  double seconds;            /* host wall time of the call */
+} ehyb_cg_info_t;
+
+/*
+ * Solve A x = b for symmetric positive definite A.  b, x: device arrays of n doubles in the ORIGINAL
+ * numbering; x holds the initial guess on entry and the solution on return.  Synchronous.
+ *   refine = 0: FP64 CG (Hestenes-Stiefel), stop when ||r_k|| <= rtol ||b|| (recursive residual)
+ *               or after max_iter iterations.
+ *   refine = 1 / 2: FP64 iterative refinement: r = b - A x in FP64, an inner CG on the values stored in
+ *               FP32 (1) / BF16 (2) with FP32 vectors and FP32 SpMV accumulation, FP64 dot products and
+ *               alpha/beta, to a relative residual inner_rtol (0 = 1e-4 for FP32, 1e-2 for BF16), then
+ *               x += d in FP64; stop when the FP64 residual <= rtol ||b||, when it stops decreasing, or
+ *               when max_iter inner iterations are spent.  The plan must hold that value copy
+ *               (opt.lowp == refine), else EHYB_ERR_UNSUPPORTED.
+ * Requires the sliced ER layout (er_layout 0).  Returns EHYB_ERR_NOT_CONVERGED (info filled) when the
+ * test was not met.  The solver workspace (5 FP64 + 4 FP32 vectors) is allocated on the first call.
+ */
+ehyb_status_t ehyb_cg(ehyb_plan_t plan, const double* b, double* x, double rtol, int32_t max_iter, int32_t refine,
+                      double inner_rtol, ehyb_cg_info_t* info, void* stream);
+
+/* r.r of the recursion for iterations 0..count-1 of the last FP64 CG solve (or of the last inner solve). */
+ehyb_status_t ehyb_cg_history(ehyb_plan_t plan, double* hist, int32_t cap, int32_t* count);
+
 /* Plan statistics; synchronises and reads the device status word. */
 ehyb_status_t ehyb_plan_info(ehyb_plan_t plan, ehyb_plan_info_t* info);
 

@@ -70,6 +70,15 @@ class PlanExport(ctypes.Structure):
                 ("er_scol", ctypes.c_void_p), ("er_sval", ctypes.c_void_p), ("row_er_count", ctypes.c_void_p)]
 
 
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 _P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 
 
@@ -92,6 +101,8 @@ _sig("ehyb_permute", [_P, _I32, _P, _P, _P])
 _sig("ehyb_spmv_host", [_P, _P, _P, _P])
 _sig("ehyb_spmv_lowp", [_P, _P, _P, _P])
 _sig("ehyb_spmv_noalloc", [_P, _P, _P, _P])
+_sig("ehyb_cg", [_P, _P, _P, _D, _I32, _I32, _D, ctypes.POINTER(CgInfo), _P])
+_sig("ehyb_cg_history", [_P, _P, _I32, ctypes.POINTER(_I32)])
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
@@ -183,6 +194,10 @@ def ehyb_spmv_noalloc(plan, x, y, stream):
     return _lib.ehyb_spmv_noalloc(plan, x, y, stream)
 
 
+def ehyb_cg(plan, b, x, rtol, max_iter, refine, inner_rtol, info: CgInfo, stream):
+    return _lib.ehyb_cg(plan, b, x, rtol, max_iter, refine, inner_rtol, ctypes.byref(info), stream)
+
+
 def ehyb_plan_check(plan):
     return _lib.ehyb_plan_check(plan)
 
@@ -252,6 +267,22 @@ class Plan:
     def spmv_noalloc(self, x, y, stream=None):
         _check(ehyb_spmv_noalloc(self._h, _dev(x, "float64"), _dev(y, "float64"), _stream(stream)),
                "ehyb_spmv_noalloc")
+
+    def cg(self, b, x, rtol: float = 1e-10, max_iter: int = 10000, refine: int = 0, inner_rtol: float = 0.0,
+           stream=None, raise_not_converged: bool = False):
+        """Solve A x = b in place on x (CUDA float64 tensors, original numbering).  Returns (status, info)."""
+        info = CgInfo()
+        st = ehyb_cg(self._h, _dev(b, "float64"), _dev(x, "float64"), float(rtol), int(max_iter), int(refine),
+                     float(inner_rtol), info, _stream(stream))
+        if st != 0 and (st != EHYB_ERR_NOT_CONVERGED or raise_not_converged):
+            raise EhybError(st, "ehyb_cg")
+        return st, info.as_dict()
+
+    def cg_history(self, cap: int = 100000) -> np.ndarray:
+        h = np.zeros(cap)
+        cnt = ctypes.c_int32(0)
+        _check(_lib.ehyb_cg_history(self._h, h.ctypes.data, cap, ctypes.byref(cnt)), "ehyb_cg_history")
+        return h[:cnt.value]
 
     def check(self) -> int:
         return int(ehyb_plan_check(self._h))

@@ -18,6 +18,7 @@
 
 #include "device.h"
 #include "plan.h"
+#include "plan_internal.h"
 
 using namespace ehyb;
 
@@ -115,32 +116,6 @@ ehyb_status_t validate_csr(int64_t nr, int64_t nc, int64_t nnz, const int64_t* r
 
 }  // namespace
 
-struct ehyb_plan_s {
-  HostPlan host;        // arrays kept only when requested (or host-only); metadata always
-  bool host_kept = false;
-  bool host_only = false;
-  DevPlan dev;
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  double* xp = nullptr;     // FP64 workspace (plan numbering), n + 2
-  float* xp32 = nullptr;    // FP32 workspace
-  double* hx = nullptr;     // device staging for ehyb_spmv_host
-  double* hy = nullptr;
-  int32_t lowp = 0;
-  int32_t er_tpr = 1;
-  int32_t er_layout = 0;
-  int64_t ell_nnz = 0, ell_stored = 0, er_rows = 0, er_nnz = 0, er_stored = 0;
-  int32_t nslices = 0, slice_rows = 0, num_sms = 0;
-  double upload_ms = 0;
-  int device = -1;
-  // profiling
-  bool prof = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
-  size_t ev_used = 0;
-  // export copies (host)
-  bool exported = false;
-};
-
 struct ehyb_csr_s {
   int64_t n = 0, nnz = 0;
   int32_t tpr = 1;
@@ -150,6 +125,9 @@ struct ehyb_csr_s {
 };
 
 namespace ehyb {
+ehyb_status_t cuda_error_status(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+ehyb_status_t device_alloc(void** p, size_t bytes) { return dev_alloc(p, bytes); }
+
 // device view of a plan for entry points defined in other translation units
 const DevPlan* plan_device_view(ehyb_plan_t plan, int* device) {
   if (!plan || plan->host_only) return nullptr;
@@ -384,12 +362,13 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
 ehyb_status_t ehyb_destroy(ehyb_plan_t p) {
   if (!p) return EHYB_OK;
   ehyb_status_t st = EHYB_OK;
-  if (p->arena || p->hx || !p->ev_pool.empty()) {
+  if (p->arena || p->hx || p->cg || !p->ev_pool.empty()) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
     if (p->arena) cudaFree(p->arena);
     if (p->hx) cudaFree(p->hx);
     if (p->hy) cudaFree(p->hy);
+    if (p->cg) cg_work_free(p->cg);
     for (auto& ev : p->ev_pool) {
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);

@@ -46,9 +46,13 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 
 // Fused slab + ER kernel.  xp is in the plan numbering; y is written at new_to_old[r] when
 // scatter != 0, else at r.
-cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s);
+// dot_part (optional, sliced ER layout only): per-block partial sums of y_r * xp_r in FP64, fixed order.
+// skip (optional): device flag; the launch returns at once while it is non-zero.
+cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s,
+                            double* dot_part = nullptr, const int32_t* skip = nullptr);
 // values stored FP32 (lowp = 1) or BF16 (lowp = 2); x, y and the accumulation in FP32
-cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s);
+cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s,
+                             double* dot_part = nullptr, const int32_t* skip = nullptr);
 
 // plain vector-CSR baseline: tpr lanes per row
 cudaError_t launch_csr_f64(int64_t n, const int64_t* rp, const int32_t* col, const double* val, const double* x,

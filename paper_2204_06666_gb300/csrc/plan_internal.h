@@ -1,0 +1,50 @@
+// Internal definition of a plan (shared by the translation units of the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "device.h"
+#include "plan.h"
+
+#include "../../include/ehyb.h"
+
+namespace ehyb {
+struct CgWork;  // solver workspace, defined in cg.cu
+void cg_work_free(CgWork* w);
+// records the CUDA error text for ehyb_last_cuda_error and returns EHYB_ERR_CUDA
+ehyb_status_t cuda_error_status(cudaError_t e, const char* what);
+// device allocation through the library's allocation hook (EHYB_ERR_OOM on failure)
+ehyb_status_t device_alloc(void** p, size_t bytes);
+}  // namespace ehyb
+
+struct ehyb_plan_s {
+  ehyb::HostPlan host;        // arrays kept only when requested (or host-only); metadata always
+  bool host_kept = false;
+  bool host_only = false;
+  ehyb::DevPlan dev;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  double* xp = nullptr;     // FP64 workspace (plan numbering), n + 2
+  float* xp32 = nullptr;    // FP32 workspace
+  double* hx = nullptr;     // device staging for ehyb_spmv_host
+  double* hy = nullptr;
+  int32_t lowp = 0;
+  int32_t er_tpr = 1;
+  int32_t er_layout = 0;
+  int64_t ell_nnz = 0, ell_stored = 0, er_rows = 0, er_nnz = 0, er_stored = 0;
+  int32_t nslices = 0, slice_rows = 0, num_sms = 0;
+  double upload_ms = 0;
+  int device = -1;
+  // profiling
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  // export copies (host)
+  bool exported = false;
+  // solver workspace (allocated by the first ehyb_cg call)
+  ehyb::CgWork* cg = nullptr;
+};
+

@@ -169,7 +169,21 @@ struct KArgs {
   int32_t* status;
   uint64_t timeout_ns;
   int32_t inject;
+  double* dot_part;       // optional: per-block partial of sum_r y_r * xp_r (fixed summation order)
+  const int32_t* skip;    // optional: the launch does nothing while *skip != 0 (converged solver)
 };
+
+// Deterministic block sum (xor-tree inside warps, warps in index order); result in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v, double* ws) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+  return s;
+}
 
 // V: stored value type; X: type of x, y and of the accumulation
 template <typename V, typename X, bool SCATTER, bool ER_SLICED>
@@ -182,6 +196,7 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
   __shared__ int stage_ok;
   constexpr int EPV = 16 / (int)sizeof(X);  // elements per 16 bytes
 
+  if (a.skip && *a.skip) return;
   const int p = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -234,6 +249,9 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
   const int rows_per_slice = 32 >> a.tpr_log2;
 
   // ---- 2. slab: warp per 32-lane slice, dynamic slice balancing inside the partition
+  // (static round-robin when the fused dot product is requested, so its order is fixed)
+  const bool dot = a.dot_part != nullptr;
+  double dacc = 0.0;
   int s = s0 + warp;
   while (s < s1) {
     const int64_t pos = a.slice_pos[s];
@@ -249,10 +267,20 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     if (sub == 0 && row < pe) {
       if (SCATTER) y[a.new_to_old[row]] = acc;
       else y[row] = acc;
+      if (dot) dacc = fma((double)acc, (double)xsl[row - pb], dacc);
     }
-    int nxt = 0;
-    if (lane == 0) nxt = atomicAdd(&slice_counter, 1);
-    s = __shfl_sync(FULL, nxt, 0);
+    if (dot) {
+      s += nwarps;
+    } else {
+      int nxt = 0;
+      if (lane == 0) nxt = atomicAdd(&slice_counter, 1);
+      s = __shfl_sync(FULL, nxt, 0);
+    }
+  }
+  if (dot) {  // only offered for the sliced ER layout, where a slice's rows are final here
+    __shared__ double ws[32];
+    const double t = block_sum_fixed(dacc, ws);
+    if (tid == 0) a.dot_part[p] = t;
   }
   if (ER_SLICED) return;
   const int e0 = a.er_part_ptr[p];
@@ -344,6 +372,8 @@ KArgs make_args(const DevPlan& P) {
   a.status = P.status;
   a.timeout_ns = P.wait_timeout_ns;
   a.inject = P.inject_wait_fault;
+  a.dot_part = nullptr;
+  a.skip = nullptr;
   return a;
 }
 
@@ -394,8 +424,10 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 
 template <typename V, typename X>
 static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const V* erv_sl, const X* xp, X* y,
-                         int scatter, size_t smem, cudaStream_t s) {
+                         int scatter, size_t smem, cudaStream_t s, double* dot_part, const int32_t* skip) {
   KArgs a = make_args(P);
+  a.dot_part = dot_part;
+  a.skip = skip;
   const bool sl = P.er_layout == 0;
   const V* erv = sl ? erv_sl : erv_csr;
   if (scatter) {
@@ -407,19 +439,23 @@ static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const 
   }
 }
 
-cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s) {
+cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s,
+                            double* dot_part, const int32_t* skip) {
   if (P.nparts == 0) return cudaSuccess;
-  launch_typed<double, double>(P, P.ell_val, P.er_val, P.er_sval, xp, y, scatter, ehyb_smem_bytes(P, 8), s);
+  launch_typed<double, double>(P, P.ell_val, P.er_val, P.er_sval, xp, y, scatter, ehyb_smem_bytes(P, 8), s, dot_part,
+                               skip);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s) {
+cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s,
+                             double* dot_part, const int32_t* skip) {
   if (P.nparts == 0) return cudaSuccess;
   const size_t smem = ehyb_smem_bytes(P, 4);
   if (lowp == 1)
-    launch_typed<float, float>(P, P.ell_val_f32, P.er_val_f32, P.er_sval_f32, xp, y, scatter, smem, s);
+    launch_typed<float, float>(P, P.ell_val_f32, P.er_val_f32, P.er_sval_f32, xp, y, scatter, smem, s, dot_part, skip);
   else
-    launch_typed<uint16_t, float>(P, P.ell_val_bf16, P.er_val_bf16, P.er_sval_bf16, xp, y, scatter, smem, s);
+    launch_typed<uint16_t, float>(P, P.ell_val_bf16, P.er_val_bf16, P.er_sval_bf16, xp, y, scatter, smem, s, dot_part,
+                                  skip);
   return cudaGetLastError();
 }
 
