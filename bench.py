@@ -49,13 +49,15 @@ WORKLOADS = {
                            desc="3D Q1 hex elasticity, 48^3 nodes x 3 dof (profiling size, 0.27 GB slab)"),
     "fem2d_p1_200": dict(kind="fem2d", N=200, seed_x=3, desc="2D P1 Laplacian, 200^2 nodes, jitter 0.3h"),
     "tet_lap3d_126": dict(kind="tet", N=126, seed_x=23, desc="3D P1 tet Laplacian, 126^3 nodes, Dirichlet"),
+    "hex_elast3d_70_clamped": dict(kind="hex", N=70, seed_x=24, clamp=True,
+                                   desc="3D Q1 hex elasticity, 70^3 nodes x 3 dof, min-z face clamped (SPD)"),
 }
 
 
 def make_matrix(w):
     import gen
     if w["kind"] == "hex":
-        return gen.hex_elast3d(N=w["N"])
+        return gen.hex_elast3d(N=w["N"], clamp_minz=w.get("clamp", False))
     if w["kind"] == "fem2d":
         return gen.fem2d_p1(N=w["N"])
     return gen.tet_lap3d(N=w["N"])
@@ -334,6 +336,149 @@ def run_ehyb(args):
     return 0
 
 
+def run_solver(args):
+    """Time to a 1e-10 relative residual: FP64 CG vs FP64 refinement around FP32 / BF16 inner CG.
+
+    b = A x* with x* ~ U[-1, 1) (seeded), computed by the library's FP64 SpMV.  Each method solves from
+    x0 = 0; one untimed solve, then the median of `--solver-reps` timed solves (host wall clock around
+    the synchronous ehyb_cg call).  Reported per method: iterations, refinements, seconds, the library's
+    FP64 true residual and the error against x* and against the FP64 CG solution.
+    """
+    import torch
+    import gen
+    import paper_2204_06666_gb300 as eh
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    w = WORKLOADS[args.workload]
+    A = make_matrix(w)
+    xstar = gen.uniform(A.n, w["seed_x"])
+    P32 = eh.Plan(A, lowp=1)
+    ex = P32.export()
+    pv = np.empty(A.n, np.int32)
+    for p in range(len(ex["part_ptr"]) - 1):
+        pv[ex["new_to_old"][ex["part_ptr"][p]:ex["part_ptr"][p + 1]]] = p
+    P16 = eh.Plan(A, lowp=2, part_vec=pv)   # same partition, BF16 value copy
+    xs = torch.from_numpy(xstar).cuda()
+    b = torch.empty_like(xs)
+    P32.spmv(xs, b)
+    torch.cuda.synchronize()
+    out = {}
+    x_ref = None
+    for name, plan, refine in (("fp64_cg", P32, 0), ("refined_fp32", P32, 1), ("refined_bf16", P16, 2)):
+        times, res = [], None
+        for rep in range(args.solver_reps + 1):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info = plan.cg(b, x, rtol=1e-10, max_iter=args.solver_max_iter, refine=refine)
+            dt = time.perf_counter() - t0
+            if rep > 0:
+                times.append(dt)
+            res = (st, info, x)
+        st, info, x = res
+        xh = x.cpu().numpy()
+        if refine == 0:
+            x_ref = xh
+        out[name] = {"status": eh.STATUS.get(st, st), "converged": bool(info["converged"]),
+                     "iterations": info["iterations"], "refinements": info["refinements"],
+                     "seconds": statistics.median(times), "relres_fp64": info["relres"],
+                     "err_vs_xstar": float(np.linalg.norm(xh - xstar) / np.linalg.norm(xstar)),
+                     "err_vs_fp64_cg": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)),
+                     "ms_per_iteration": 1e3 * statistics.median(times) / max(info["iterations"], 1)}
+    base = out["fp64_cg"]["seconds"]
+    line = {"metric": "CG time to 1e-10 relative residual (FP64 vs mixed-precision refinement)", "unit": "s",
+            "value": out["refined_fp32"]["seconds"], "higher_is_better": False, "n_gpus": 1, "dtype": "f64+f32",
+            "data": "synthetic", "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "desc": w["desc"],
+                                             "reps": args.solver_reps},
+            "methods": out,
+            "speedup_vs_fp64": {k: base / v["seconds"] for k, v in out.items() if v["converged"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _event_time(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batch(args):
+    """64 generated FEM matrices (n log-uniform in [5k, 300k], four element kinds): one persistent batch
+    launch (graph replay) vs the same 64 SpMVs issued one by one."""
+    import torch
+    import gen
+    import paper_2204_06666_gb300 as eh
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    mats = gen.fem_batch(count=args.batch_count, seed=31)
+    plans = [eh.Plan(A) for A in mats]
+    xs = [torch.from_numpy(gen.uniform(A.n, 32 + i)).cuda() for i, A in enumerate(mats)]
+    ys = [torch.empty_like(x) for x in xs]
+    B = eh.Batch(plans)
+    for _ in range(args.warmup):
+        B.spmv(xs, ys)
+    t_batch = _event_time(lambda: B.spmv(xs, ys), args.steps, stream)
+
+    def one_by_one():
+        for P, x, y in zip(plans, xs, ys):
+            P.spmv(x, y)
+    for _ in range(args.warmup):
+        one_by_one()
+    t_seq = _event_time(one_by_one, max(3, args.steps // 4), stream)
+    nnz = sum(A.nnz for A in mats)
+    byts = sum(P.info()["bytes_effective"] for P in plans)
+    line = {"metric": "batched EHYB SpMV GFLOP/s (64 FEM matrices, one persistent graph-captured launch)",
+            "unit": "GFLOP/s", "value": 2 * nnz / t_batch / 1e6, "higher_is_better": True, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"fem_batch_{args.batch_count}", "matrices": len(mats),
+                       "rows": sum(A.n for A in mats), "nnz": nnz, "n_min": min(A.n for A in mats),
+                       "n_max": max(A.n for A in mats), "kinds": sorted(set(A.name.split("_N")[0] for A in mats)),
+                       "tiles": B.info()["tiles"], "grid": B.info()["grid"]},
+            "batch": {"ms": t_batch, "gflops": 2 * nnz / t_batch / 1e6, "effective_gbs": byts / t_batch / 1e6},
+            "one_by_one": {"ms": t_seq, "gflops": 2 * nnz / t_seq / 1e6, "effective_gbs": byts / t_seq / 1e6,
+                           "launches": 2 * len(mats)},
+            "speedup": t_seq / t_batch}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_spmm(args):
+    """SpMM with k = 8 and 32 right-hand sides on the 70^3 hex matrix vs k separate SpMVs."""
+    import torch
+    import gen
+    import paper_2204_06666_gb300 as eh
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    A = make_matrix(WORKLOADS["hex_elast3d_70"])
+    P = eh.Plan(A)
+    x = torch.from_numpy(gen.uniform(A.n, 13)).cuda()
+    y = torch.empty_like(x)
+    t_spmv = _event_time(lambda: P.spmv(x, y), 50, stream)
+    out = {}
+    for k in args.spmm_k:
+        X = torch.from_numpy(np.stack([gen.uniform(A.n, 32 + j) for j in range(k)], axis=1)).cuda()
+        Y = torch.empty_like(X)
+        for _ in range(args.warmup):
+            P.spmm(X, Y)
+        t = _event_time(lambda: P.spmm(X, Y), max(5, args.steps // 50), stream)
+        flops = 2.0 * A.nnz * k
+        out[f"k{k}"] = {"ms": t, "gflops": flops / t / 1e6, "fp64_roof_frac": flops / t / 1e9 / FP64_PEAK_TFLOPS,
+                        "vs_k_spmv": (k * t_spmv) / t}
+    line = {"metric": "EHYB SpMM GFLOP/s (FP64, k right-hand sides, 3D hex 70^3)", "unit": "GFLOP/s",
+            "value": out[f"k{args.spmm_k[0]}"]["gflops"], "higher_is_better": True, "n_gpus": 1, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "hex_elast3d_70", "n": A.n, "nnz": A.nnz},
+            "spmv_ms": t_spmv, "spmm": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _reorder(A, n2o, o2n):
     """P A P^T in CSR, rows in the plan numbering (columns relabelled, order kept)."""
     import gen
@@ -361,11 +506,24 @@ def main():
     ap.add_argument("--skip-csr", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--solver", action="store_true", help="time CG / refined CG instead of the SpMV")
+    ap.add_argument("--batch", action="store_true", help="time the batched launch over generated FEM matrices")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--spmm", action="store_true", help="time SpMM with --spmm-k right-hand sides")
+    ap.add_argument("--spmm-k", type=int, nargs="+", default=[8, 32])
+    ap.add_argument("--solver-reps", type=int, default=3)
+    ap.add_argument("--solver-max-iter", type=int, default=50000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.solver:
+        return run_solver(args)
+    if args.batch:
+        return run_batch(args)
+    if args.spmm:
+        return run_spmm(args)
     return run_ehyb(args)
 
 

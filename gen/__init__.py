@@ -202,3 +202,28 @@ def random_csr(n: int, seed: int, mean_row: float = 8.0, int_values: bool = Fals
 def int_vector(n: int, seed: int, lo: int = -8, hi: int = 8) -> np.ndarray:
     """Small-integer vector (exact in every precision the path uses)."""
     return np.random.default_rng(seed).integers(lo, hi + 1, n).astype(np.float64)
+
+
+BATCH_KINDS = ("fem2d_p1", "tet_lap3d", "hex_lap3d", "hex_elast3d")
+
+
+def fem_batch(count: int = 64, seed: int = 31, n_min: int = 5000, n_max: int = 300000):
+    """`count` FEM matrices with row counts log-uniform in [n_min, n_max] and a kind drawn uniformly among
+    2D P1 (7/row), 3D P1 tet (15/row), 3D Q1 scalar hex (27/row) and 3D Q1 hex elasticity (81/row);
+    each jittered and relabelled with its own seeds."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        kind = BATCH_KINDS[int(rng.integers(0, 4))]
+        s_mesh, s_perm = 1000 + 2 * i + 10000 * seed, 1001 + 2 * i + 10000 * seed
+        if kind == "fem2d_p1":
+            A = fem2d_p1(N=max(2, int(round(n ** 0.5))), seed_mesh=s_mesh, seed_perm=s_perm)
+        elif kind == "tet_lap3d":
+            A = tet_lap3d(N=max(2, int(round(n ** (1 / 3)))), seed_mesh=s_mesh, seed_perm=s_perm, dirichlet=False)
+        elif kind == "hex_lap3d":
+            A = hex_lap3d(N=max(2, int(round(n ** (1 / 3)))), seed_mesh=s_mesh, seed_perm=s_perm)
+        else:
+            A = hex_elast3d(N=max(2, int(round((n / 3) ** (1 / 3)))), seed_mesh=s_mesh, seed_perm=s_perm)
+        out.append(A)
+    return out

@@ -181,6 +181,15 @@ ehyb_status_t ehyb_spmv_noalloc(ehyb_plan_t plan, const double* x, double* y, vo
  * device arrays in the original numbering.  EHYB_ERR_UNSUPPORTED if the plan has no lowp copy. */
 ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t plan, const float* x, float* y, void* stream);
 
+/*
+ * Y = A X for k right-hand sides in FP64: X and Y are row-major n x k device arrays (original
+ * numbering).  The columns run in chunks of KC in {8, 4, 2, 1} (the largest that divides k and whose
+ * KC-wide slice of X fits a block's shared memory), one launch per chunk, after one gather of X into a
+ * chunk-major workspace (n x k doubles, allocated by the first call).  Column j of Y equals ehyb_spmv of
+ * column j of X bit for bit.  Requires the sliced ER layout.  Asynchronous on `stream`.
+ */
+ehyb_status_t ehyb_spmm(ehyb_plan_t plan, int32_t k, const double* X, double* Y, void* stream);
+
 /* ---- conjugate gradients on a plan (Sec. 6: SpMV-dominated iterative solvers) ---- */
 
 typedef struct {
@@ -212,6 +221,31 @@ ehyb_status_t ehyb_cg(ehyb_plan_t plan, const double* b, double* x, double rtol,
 
 /* r.r of the recursion for iterations 0..count-1 of the last FP64 CG solve (or of the last inner solve). */
 ehyb_status_t ehyb_cg_history(ehyb_plan_t plan, double* hist, int32_t cap, int32_t* count);
+
+/* ---- batching: many plans in one persistent launch ---- */
+
+typedef struct ehyb_batch_s* ehyb_batch_t;
+
+/*
+ * Group `count` plans (FP64, sliced ER layout, all on the current device) for ehyb_batch_spmv.  The
+ * batch keeps pointers to the plans: destroy the batch before any of its plans.  Its work list is the
+ * (plan, partition) pairs ordered by stored slots, largest first.
+ */
+ehyb_status_t ehyb_batch_create(int32_t count, const ehyb_plan_t* plans, ehyb_batch_t* out);
+
+/*
+ * ys[i] = A_i xs[i] for every plan of the batch (device arrays, original numbering), asynchronously on
+ * `stream`: one gather launch over all plans and one persistent launch whose blocks pull partitions
+ * from a shared queue, both replayed from a CUDA graph captured on the first call.  Results equal
+ * ehyb_spmv on each plan bit for bit.  Uses the plans' workspaces: do not overlap with other calls on
+ * the same plans.  xs / ys are host arrays of `count` device pointers.
+ */
+ehyb_status_t ehyb_batch_spmv(ehyb_batch_t batch, const double* const* xs, double* const* ys, void* stream);
+
+/* Work list length, persistent grid size and threads per block of the batch launch. */
+ehyb_status_t ehyb_batch_info(ehyb_batch_t batch, int32_t* ntiles, int32_t* grid, int32_t* threads);
+
+ehyb_status_t ehyb_batch_destroy(ehyb_batch_t batch);  /* NULL is accepted */
 
 /* Plan statistics; synchronises and reads the device status word. */
 ehyb_status_t ehyb_plan_info(ehyb_plan_t plan, ehyb_plan_info_t* info);

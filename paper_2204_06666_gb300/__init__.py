@@ -101,8 +101,13 @@ _sig("ehyb_permute", [_P, _I32, _P, _P, _P])
 _sig("ehyb_spmv_host", [_P, _P, _P, _P])
 _sig("ehyb_spmv_lowp", [_P, _P, _P, _P])
 _sig("ehyb_spmv_noalloc", [_P, _P, _P, _P])
+_sig("ehyb_spmm", [_P, _I32, _P, _P, _P])
 _sig("ehyb_cg", [_P, _P, _P, _D, _I32, _I32, _D, ctypes.POINTER(CgInfo), _P])
 _sig("ehyb_cg_history", [_P, _P, _I32, ctypes.POINTER(_I32)])
+_sig("ehyb_batch_create", [_I32, _P, ctypes.POINTER(_P)])
+_sig("ehyb_batch_spmv", [_P, _P, _P, _P])
+_sig("ehyb_batch_info", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
+_sig("ehyb_batch_destroy", [_P])
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
@@ -268,6 +273,13 @@ class Plan:
         _check(ehyb_spmv_noalloc(self._h, _dev(x, "float64"), _dev(y, "float64"), _stream(stream)),
                "ehyb_spmv_noalloc")
 
+    def spmm(self, X, Y, stream=None):
+        """Y = A X for row-major (n, k) CUDA float64 tensors."""
+        if X.dim() != 2 or X.shape != Y.shape or X.shape[0] != self.n:
+            raise ValueError("X and Y must both be (n, k)")
+        _check(_lib.ehyb_spmm(self._h, int(X.shape[1]), _dev(X, "float64"), _dev(Y, "float64"), _stream(stream)),
+               "ehyb_spmm")
+
     def cg(self, b, x, rtol: float = 1e-10, max_iter: int = 10000, refine: int = 0, inner_rtol: float = 0.0,
            stream=None, raise_not_converged: bool = False):
         """Solve A x = b in place on x (CUDA float64 tensors, original numbering).  Returns (status, info)."""
@@ -355,5 +367,38 @@ class CsrBaseline:
         try:
             if self._h:
                 _lib.ehyb_csr_destroy(self._h)
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several plans run by one persistent launch (ehyb_batch_*); keeps the plans alive."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        self._h = ctypes.c_void_p()
+        _check(_lib.ehyb_batch_create(len(self.plans), arr, ctypes.byref(self._h)), "ehyb_batch_create")
+
+    def spmv(self, xs, ys, stream=None):
+        n = len(self.plans)
+        xa = (ctypes.c_void_p * n)(*[_dev(x, "float64") for x in xs])
+        ya = (ctypes.c_void_p * n)(*[_dev(y, "float64") for y in ys])
+        _check(_lib.ehyb_batch_spmv(self._h, xa, ya, _stream(stream)), "ehyb_batch_spmv")
+
+    def info(self) -> dict:
+        t, g, th = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(_lib.ehyb_batch_info(self._h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(th)), "ehyb_batch_info")
+        return {"tiles": t.value, "grid": g.value, "threads": th.value}
+
+    def close(self):
+        if self._h:
+            _check(_lib.ehyb_batch_destroy(self._h), "ehyb_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.ehyb_batch_destroy(self._h)
         except Exception:
             pass

@@ -362,13 +362,14 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
 ehyb_status_t ehyb_destroy(ehyb_plan_t p) {
   if (!p) return EHYB_OK;
   ehyb_status_t st = EHYB_OK;
-  if (p->arena || p->hx || p->cg || !p->ev_pool.empty()) {
+  if (p->arena || p->hx || p->cg || p->spmm_ws || !p->ev_pool.empty()) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
     if (p->arena) cudaFree(p->arena);
     if (p->hx) cudaFree(p->hx);
     if (p->hy) cudaFree(p->hy);
     if (p->cg) cg_work_free(p->cg);
+    if (p->spmm_ws) cudaFree(p->spmm_ws);
     for (auto& ev : p->ev_pool) {
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);

@@ -1,0 +1,366 @@
+// Device code shared by the EHYB kernels (per-plan launch and persistent batch launch), sm_103a.
+//
+// partition_spmv: Alg. 3 re-designed for GB300.  One thread block works on one partition at a time
+//   (the paper's "block = partition", Sec. 3.2):
+//     1. thread 0 issues ONE bulk asynchronous copy (cp.async.bulk, completion counted on an
+//        mbarrier) of the partition's slice of x into shared memory: CachedVec of Alg. 3;
+//        a ragged unaligned tail (at most 15 bytes) is fetched with plain loads;
+//     2. thread 0 waits on the mbarrier with a time bound (on expiry the block records
+//        EHYB_ERR_TIMEOUT in the plan status word and returns);
+//     3. each warp takes 32-lane slices of the partition from a shared counter (the dynamic
+//        slice balancing of Alg. 3) and runs y[row] = sum_k ValELL * CachedVec[ColELL] with the
+//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot, eight slots of
+//        values and columns loaded ahead of their FMAs to keep enough bytes in flight;
+//     4. extra-row (ER) entries, two layouts:
+//        - sliced (er_layout 0, default): the ER entries of the slice's own rows are stored in
+//          the same lane -> row arrangement right behind it (the paper stores its ER part as
+//          stride-32 slices too, Alg. 2); the warp continues with them, gathering x from global
+//          memory, and writes y once -- no block barrier, no read-modify-write, no FP64 shuffle;
+//        - CSR lines (er_layout 1): after a block barrier, er_tpr lanes per ER line with a
+//          shuffle reduction, y[yIdxER] += sum.
+//   In both layouts the rows a block updates are its own, so the paper's second pass over ER
+//   slices from a global counter is not needed: no atomics on y, deterministic results.
+#pragma once
+#include <cstdint>
+
+#include "device.h"
+
+namespace ehyb {
+namespace core {
+
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kTimeoutCode = 9;  // EHYB_ERR_TIMEOUT
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: true when phase `parity` completed within limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float(((uint32_t)h) << 16); }
+
+template <typename V, typename X>
+__device__ __forceinline__ X load_val(const V* p);
+template <>
+__device__ __forceinline__ double load_val<double, double>(const double* p) {
+  return __ldcs(p);
+}
+template <>
+__device__ __forceinline__ float load_val<float, float>(const float* p) {
+  return __ldcs(p);
+}
+template <>
+__device__ __forceinline__ float load_val<uint16_t, float>(const uint16_t* p) {
+  return bf16_to_f32(__ldcs(reinterpret_cast<const unsigned short*>(p)));
+}
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+constexpr int kBatch = 8;  // slots whose loads are issued before their FMAs
+
+// acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory
+template <typename V, typename X>
+__device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
+                                      const X* xs, X acc) {
+  int k = 0;
+  for (; k + kBatch <= w; k += kBatch) {
+    X v[kBatch];
+    int c[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
+      c[u] = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u)));
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) acc = fma_t(v[u], xs[c[u]], acc);
+  }
+  for (; k < w; ++k)
+    acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k),
+                xs[__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)k))], acc);
+  return acc;
+}
+
+// acc += sum_{k<w} v[32k] * xg[c[32k]]: sliced extra-row slots of one lane, x from global memory
+template <typename V, typename X>
+__device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __restrict__ cp, int w,
+                                    const X* __restrict__ xg, X acc) {
+  int k = 0;
+  for (; k + kBatch <= w; k += kBatch) {
+    X v[kBatch];
+    int c[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
+      c[u] = __ldcs(cp + 32 * (int64_t)(k + u));
+    }
+    X xv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) xv[u] = __ldg(xg + c[u]);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) acc = fma_t(v[u], xv[u], acc);
+  }
+  for (; k < w; ++k) acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k), __ldg(xg + __ldcs(cp + 32 * (int64_t)k)), acc);
+  return acc;
+}
+
+struct KArgs {
+  int32_t tpr_log2, er_tpr_log2;
+  const int64_t* er_slice_pos;
+  const int32_t* er_scol;
+  const int32_t* new_to_old;
+  const int32_t* part_ptr;
+  const int32_t* slice_ptr;
+  const int64_t* slice_pos;
+  const uint16_t* ell_col;
+  const int32_t* er_part_ptr;
+  const int32_t* er_row;
+  const int64_t* er_ptr;
+  const int32_t* er_col;
+  int32_t* status;
+  uint64_t timeout_ns;
+  int32_t inject;
+  double* dot_part;       // optional: per-block partial of sum_r y_r * xp_r (fixed summation order)
+  const int32_t* skip;    // optional: the launch does nothing while *skip != 0 (converged solver)
+};
+
+// Deterministic block sum (xor-tree inside warps, warps in index order); result in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v, double* ws) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+  return s;
+}
+
+// V: stored value type; X: type of x, y and of the accumulation
+// Shared state of one block; a block may run several partitions one after the other.
+struct BlockState {
+  uint64_t bar;        // mbarrier counting the bytes of the bulk staging copy
+  uint32_t phase;      // phases of bar completed so far
+  int bar_ready;       // bar has been initialised
+  int slice_counter;   // next slice of the current partition
+  int stage_ok;
+  double ws[32];
+};
+
+// One partition p of a plan: stage its slice of x_p, run its slab (and ER) slices, write y.
+// Returns false (uniformly across the block) when the staging wait ran out of time.
+template <typename V, typename X, bool SCATTER, bool ER_SLICED>
+__device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
+                                               const V* __restrict__ er_val, const X* __restrict__ xp,
+                                               X* __restrict__ y, const int p, X* xs, BlockState& bs) {
+  constexpr int EPV = 16 / (int)sizeof(X);  // elements per 16 bytes
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int pb = a.part_ptr[p];
+  const int pe = a.part_ptr[p + 1];
+  const int s0 = a.slice_ptr[p];
+  const int s1 = a.slice_ptr[p + 1];
+
+  // ---- 1. stage x_p[pb, pe) into shared memory
+  const int a0 = pb & ~(EPV - 1);  // 16-byte aligned start
+  const int a1 = pe & ~(EPV - 1);  // bulk part ends at the last aligned boundary <= pe
+  const bool aligned_src = ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
+  const uint32_t bulk_bytes = (aligned_src && a1 > a0) ? (uint32_t)(a1 - a0) * (uint32_t)sizeof(X) : 0u;
+  if (tid == 0) {
+    bs.slice_counter = s0 + nwarps;
+    if (bulk_bytes) {
+      if (!bs.bar_ready) {
+        mbar_init(&bs.bar, 1);
+        bs.bar_ready = 1;
+      }
+      // order this block's earlier generic-proxy use of the buffer before the async-proxy copy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(&bs.bar, bulk_bytes);
+      if (!a.inject) bulk_g2s(xs, xp + a0, bulk_bytes, &bs.bar);
+    }
+  }
+  // plain loads: everything when the source is unaligned, else the ragged tail [a1, pe)
+  {
+    const int lo = bulk_bytes ? (a1 > pb ? a1 : pb) : pb;
+    for (int i = lo + tid; i < pe; i += blockDim.x) xs[i - a0] = xp[i];
+  }
+  if (tid == 0) {
+    int ok = 1;
+    if (bulk_bytes) {
+      const uint32_t par = bs.phase & 1u;
+      ok = mbar_wait_bounded(&bs.bar, par, a.timeout_ns) ? 1 : 0;
+      if (!ok) {
+        atomicCAS(a.status, 0, kTimeoutCode);
+        // a copy that was issued must land before the block's shared memory goes away
+        if (!a.inject) mbar_wait_bounded(&bs.bar, par, a.timeout_ns);
+      }
+      bs.phase += 1;
+    }
+    bs.stage_ok = ok;
+  }
+  __syncthreads();
+  if (!bs.stage_ok) return false;
+  // every thread observes the completed phase itself (acquire of the bulk-copy writes)
+  if (bulk_bytes) (void)mbar_try_wait(&bs.bar, (bs.phase - 1u) & 1u);
+
+  const X* xsl = xs + (pb - a0);  // xsl[local column] = x_p[pb + local column]
+  const int tpr = 1 << a.tpr_log2;
+  const int sub = lane & (tpr - 1);
+  const int rows_per_slice = 32 >> a.tpr_log2;
+
+  // ---- 2. slab: warp per 32-lane slice, dynamic slice balancing inside the partition
+  // (static round-robin when the fused dot product is requested, so its order is fixed)
+  const bool dot = a.dot_part != nullptr;
+  double dacc = 0.0;
+  int s = s0 + warp;
+  while (s < s1) {
+    const int64_t pos = a.slice_pos[s];
+    const int w = (int)((a.slice_pos[s + 1] - pos) >> 5);
+    X acc = slab_dot<V, X>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
+    if (ER_SLICED) {
+      const int64_t epos = a.er_slice_pos[s];
+      const int we = (int)((a.er_slice_pos[s + 1] - epos) >> 5);
+      acc = er_dot<V, X>(er_val + epos + lane, a.er_scol + epos + lane, we, xp, acc);
+    }
+    for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
+    if (sub == 0 && row < pe) {
+      if (SCATTER) y[a.new_to_old[row]] = acc;
+      else y[row] = acc;
+      if (dot) dacc = fma((double)acc, (double)xsl[row - pb], dacc);
+    }
+    if (dot) {
+      s += nwarps;
+    } else {
+      int nxt = 0;
+      if (lane == 0) nxt = atomicAdd(&bs.slice_counter, 1);
+      s = __shfl_sync(FULL, nxt, 0);
+    }
+  }
+  if (dot) {  // only offered for the sliced ER layout, where a slice's rows are final here
+    const double t = block_sum_fixed(dacc, bs.ws);
+    if (tid == 0) a.dot_part[p] = t;
+  }
+  if (ER_SLICED) return true;
+  const int e0 = a.er_part_ptr[p];
+  const int e1 = a.er_part_ptr[p + 1];
+  if (e0 == e1) return true;
+  __syncthreads();  // slab results of this block are visible before the ER updates
+
+  // ---- 3. ER lines of this partition: er_tpr lanes per line, shuffle reduction
+  const int etpr = 1 << a.er_tpr_log2;
+  const int esub = lane & (etpr - 1);
+  const int lines_per_warp = 32 >> a.er_tpr_log2;
+  for (int eb = e0 + warp * lines_per_warp; eb < e1; eb += nwarps * lines_per_warp) {
+    const int e = eb + (lane >> a.er_tpr_log2);
+    X acc = X(0);
+    if (e < e1) {
+      const int64_t k1 = a.er_ptr[e + 1];
+      int64_t k = a.er_ptr[e] + esub;
+      for (; k + 3 * etpr < k1; k += 4 * etpr) {  // four entries' loads in flight
+        X v[4], xv[4];
+        int c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = load_val<V, X>(er_val + k + u * etpr);
+          c[u] = __ldcs(a.er_col + k + u * etpr);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = __ldg(xp + c[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fma_t(v[u], xv[u], acc);
+      }
+      for (; k < k1; k += etpr) acc = fma_t(load_val<V, X>(er_val + k), __ldg(xp + __ldcs(a.er_col + k)), acc);
+    }
+    for (int off = etpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if (esub == 0 && e < e1) {
+      const int row = a.er_row[e];
+      if (SCATTER) y[a.new_to_old[row]] += acc;
+      else y[row] += acc;
+    }
+  }
+  return true;
+}
+
+// host helpers
+inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << (l + 1)) <= v) ++l;
+  return l;
+}
+
+inline KArgs make_kargs(const DevPlan& P) {
+  KArgs a;
+  a.tpr_log2 = ilog2(P.tpr);
+  a.er_tpr_log2 = ilog2(P.er_tpr);
+  a.er_slice_pos = P.er_slice_pos;
+  a.er_scol = P.er_scol;
+  a.new_to_old = P.new_to_old;
+  a.part_ptr = P.part_ptr;
+  a.slice_ptr = P.slice_ptr;
+  a.slice_pos = P.slice_pos;
+  a.ell_col = P.ell_col;
+  a.er_part_ptr = P.er_part_ptr;
+  a.er_row = P.er_row;
+  a.er_ptr = P.er_ptr;
+  a.er_col = P.er_col;
+  a.status = P.status;
+  a.timeout_ns = P.wait_timeout_ns;
+  a.inject = P.inject_wait_fault;
+  a.dot_part = nullptr;
+  a.skip = nullptr;
+  return a;
+}
+
+}  // namespace core
+}  // namespace ehyb

@@ -46,5 +46,8 @@ struct ehyb_plan_s {
   bool exported = false;
   // solver workspace (allocated by the first ehyb_cg call)
   ehyb::CgWork* cg = nullptr;
+  // SpMM workspace: X gathered into the chunk-major plan numbering (allocated by ehyb_spmm)
+  void* spmm_ws = nullptr;
+  size_t spmm_ws_bytes = 0;
 };
 
