@@ -78,6 +78,8 @@ typedef struct {
   uint64_t seed;             /* reserved for randomised partitioners; the in-house one is deterministic */
   int32_t er_layout;         /* extra rows: 0 = sliced with the slab's own slices (one pass per slice, default),
                                 1 = CSR lines, er_tpr lanes each with a shuffle reduction, after a block barrier */
+  int32_t part_nnz;          /* when slice_rows is 0: size partitions for about this many entries each (capped by
+                                shared memory) instead of Eq. 1's one-per-SM split; for plans run in a batch */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;
@@ -194,7 +196,7 @@ ehyb_status_t ehyb_spmm(ehyb_plan_t plan, int32_t k, const double* X, double* Y,
 
 typedef struct {
   int32_t iterations;        /* CG iterations (refinement: inner iterations summed over the outer steps) */
-  int32_t refinements;       /* outer FP64 residual corrections (refine != 0) */
+  int32_t refinements;       /* FP64 residual corrections (refine != 0) */
   int32_t converged;         /* 1 when the stopping test was met */
   int32_t pad;
   double relres;             /* ||b - A x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
@@ -213,6 +215,11 @@ typedef struct {
  *               x += d in FP64; stop when the FP64 residual <= rtol ||b||, when it stops decreasing, or
  *               when max_iter inner iterations are spent.  The plan must hold that value copy
  *               (opt.lowp == refine), else EHYB_ERR_UNSUPPORTED.
+ *   refine = 3 / 4: FP64 residual replacement around one low-precision CG (values FP32 (3) / BF16 (4),
+ *               plan with opt.lowp = 1 / 2): the inner iteration keeps its search direction; each time
+ *               its residual has dropped by the factor inner_rtol (0 = 0.1), x += s d in FP64, the
+ *               residual is recomputed in FP64 and the iteration continues on it (direction rescaled,
+ *               not restarted).  Stops on the FP64 residual <= rtol ||b|| or max_iter iterations.
  * Requires the sliced ER layout (er_layout 0).  Returns EHYB_ERR_NOT_CONVERGED (info filled) when the
  * test was not met.  The solver workspace (5 FP64 + 4 FP32 vectors) is allocated on the first call.
  */

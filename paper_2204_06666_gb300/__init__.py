@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_PKG, "libehyb.so")
+# EHYB_LIBRARY: path of another build of the same library (e.g. one compiled with different options)
+_LIB_PATH = os.environ.get("EHYB_LIBRARY") or os.path.join(_PKG, "libehyb.so")
 
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'` "
@@ -43,7 +44,7 @@ class Options(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("smem_budget", ctypes.c_int32),
                 ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
                 ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("er_layout", ctypes.c_int32)]
+                ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -183,6 +183,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     return EHYB_ERR_INVALID_ARG;
   if (opt.er_layout < 0 || opt.er_layout > 1) return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
+      opt.part_nnz < 0 ||
       opt.num_sms < 0 || opt.wait_timeout_ns < 0)
     return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows > 65536) return EHYB_ERR_TOO_LARGE;
@@ -212,6 +213,11 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   prm.n = n;
   // Eq. 1 / Eq. 2 with tau = 8 (FP64 x slice), keeping 32 bytes of rounding and alignment slack
   prm.slice_rows = opt.slice_rows > 0 ? opt.slice_rows : eq1_slice_rows(n, 8, d.sms, budget - 32);
+  if (opt.slice_rows == 0 && opt.part_nnz > 0 && n > 0) {  // size partitions by work instead
+    const int64_t max_rows = std::min<int64_t>(65536, (budget - 32) / 8 - 2);
+    const int64_t rows = nnz > 0 ? ((int64_t)opt.part_nnz * n + nnz - 1) / nnz : n;
+    prm.slice_rows = (int32_t)std::max<int64_t>(1, std::min<int64_t>(rows, max_rows));
+  }
   prm.ell_width_cap = opt.ell_width_cap;
   prm.ell_tpr = opt.ell_tpr;
   prm.lowp = opt.lowp;

@@ -4,11 +4,11 @@
 // All vectors live in the plan's numbering (b and x are permuted once in and once out).  One CG
 // iteration is three kernels:
 //   K1  q = A p on the EHYB kernel, with p . q accumulated in its epilogue (p_r is already in shared
-//       memory) into one partial per partition;
-//   K2  alpha = (r.r) / (p.q); x += alpha p; r -= alpha q; partial sums of the new r.r;
-//   K3  beta = r.r(new) / r.r(old); p = r + beta p; the last block to finish stores r.r(new) in the
-//       history, advances the device iteration counter and raises `done` at convergence (or at the
-//       iteration limit).
+//       memory): one partial per partition, reduced into one scalar by the last block to finish;
+//   K2  alpha = (r.r) / (p.q) (once per block); x += alpha p; r -= alpha q; partial sums of the new r.r;
+//       the last block reduces them, stores r.r(new) in the history, computes beta = r.r(new) / r.r(old),
+//       advances the device iteration counter and raises `done` at convergence or at the limit;
+//   K3  p = r + beta p.
 // alpha and beta never leave the device.  Every reduction runs in a fixed order, so a solve is bit-
 // reproducible.  Once `done` is up the remaining kernels of a chunk return at once, so the iteration
 // count is exact although the host looks at the flag only once per chunk.  A chunk of kChunk
@@ -38,16 +38,16 @@ constexpr int kChunk = 16;
 }  // namespace
 
 struct CgState {
-  int32_t it, done, converged, arrive;
-  int32_t max_iter, pad0;
-  double tol2;
+  int32_t it, done, converged, arrive_dot;
+  int32_t arrive_rr, max_iter, breakdown, pad;
+  double tol2, pq, beta, grow_limit;
 };
 
 struct CgWork {
   int64_t n = 0;
   int32_t nparts = 0, hist_cap = 0;
   void* arena = nullptr;
-  double *bp = nullptr, *xp = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+  double *bp = nullptr, *xp = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *xs = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
   double *part_a = nullptr, *part_b = nullptr, *pq_part = nullptr, *hist = nullptr;
   CgState* st = nullptr;
@@ -133,68 +133,117 @@ __global__ void init_finish_kernel(const double* part_a, int na, const double* p
   if (threadIdx.x == 0) {
     hist[0] = rr;
     st->tol2 = rtol2 * (relative_to_r0 ? rr : bb);
+    st->grow_limit = 1e12 * rr;
     st->it = 0;
-    st->arrive = 0;
+    st->arrive_dot = 0;
+    st->arrive_rr = 0;
+    st->breakdown = 0;
     st->max_iter = max_iter;
     st->converged = rr <= st->tol2 ? 1 : 0;
     st->done = (st->converged || max_iter <= 0) ? 1 : 0;
   }
 }
 
-// K2: alpha = hist[it] / (p.q); x += alpha p; r -= alpha q; partials of r.r
-template <typename TV, typename TX>
-__global__ void update_kernel(int64_t n, TX* x, const TV* __restrict__ p, const TV* __restrict__ q, TV* r,
-                              const double* pq_part, int npq, const double* hist, const CgState* st,
-                              double* rr_part) {
+template <typename T> struct Vec16;
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <typename T> __device__ __forceinline__ T& lane_of(typename Vec16<T>::type& v, int i) {
+  return reinterpret_cast<T*>(&v)[i];
+}
+
+// K2: alpha = hist[it] / (p.q); x += alpha p; r -= alpha q; r.r(new) by the last block, which also
+// stores it, computes beta and advances the iteration.  16-byte vector accesses (the workspace vectors
+// are 256-byte aligned), scalar tail.  p.q <= 0 means the operator is not positive definite along p:
+// the iteration stops with `breakdown` set and nothing updated.
+template <typename T>
+__global__ void update_kernel(int64_t n, T* x, const T* __restrict__ p, const T* __restrict__ q, T* r,
+                              double* hist, CgState* st, double* rr_part) {
   if (st->done) return;
+  using V = typename Vec16<T>::type;
+  constexpr int NV = Vec16<T>::N;
   __shared__ double alpha_s;
-  if (threadIdx.x < 32) {
-    const double pq = warp_sum(pq_part, npq);
-    if (threadIdx.x == 0) alpha_s = hist[st->it] / pq;
-  }
+  __shared__ int last_s;
+  if (threadIdx.x == 0) alpha_s = st->pq > 0.0 ? hist[st->it] / st->pq : 0.0;
   __syncthreads();
-  const TV a = (TV)alpha_s;
+  if (!(alpha_s > 0.0) && hist[st->it] > 0.0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->breakdown = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  const T a = (T)alpha_s;
   double acc = 0.0;
-  for (int64_t i = gtid(); i < n; i += gstride()) {
+  const int64_t nv = n / NV;
+  for (int64_t j = gtid(); j < nv; j += gstride()) {
+    V xv = reinterpret_cast<V*>(x)[j];
+    const V pv = reinterpret_cast<const V*>(p)[j];
+    const V qv = reinterpret_cast<const V*>(q)[j];
+    V rv = reinterpret_cast<V*>(r)[j];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      V& xx = xv;
+      lane_of<T>(xx, u) = fma(a, lane_of<T>(const_cast<V&>(pv), u), lane_of<T>(xx, u));
+      const T ri = fma(-a, lane_of<T>(const_cast<V&>(qv), u), lane_of<T>(rv, u));
+      lane_of<T>(rv, u) = ri;
+      acc = fma((double)ri, (double)ri, acc);
+    }
+    reinterpret_cast<V*>(x)[j] = xv;
+    reinterpret_cast<V*>(r)[j] = rv;
+  }
+  for (int64_t i = nv * NV + gtid(); i < n; i += gstride()) {
     x[i] = fma(a, p[i], x[i]);
-    const TV ri = fma(-a, q[i], r[i]);
+    const T ri = fma(-a, q[i], r[i]);
     r[i] = ri;
     acc = fma((double)ri, (double)ri, acc);
   }
   const double s = block_sum(acc);
-  if (threadIdx.x == 0) rr_part[blockIdx.x] = s;
+  if (threadIdx.x == 0) {
+    rr_part[blockIdx.x] = s;
+    __threadfence();
+    last_s = atomicAdd(&st->arrive_rr, 1) == (int)gridDim.x - 1;  // every block has read st->it
+  }
+  __syncthreads();
+  if (last_s && threadIdx.x < 32) {
+    __threadfence();
+    const double rrn = warp_sum(rr_part, (int)gridDim.x);
+    if (threadIdx.x == 0) {
+      const int k = st->it;
+      hist[k + 1] = rrn;
+      st->beta = rrn / hist[k];
+      st->arrive_rr = 0;
+      st->it = k + 1;
+      if (rrn <= st->tol2) {
+        st->converged = 1;
+        st->done = 1;
+      } else if (!(rrn <= st->grow_limit)) {  // non-finite or diverging: stop this inner iteration
+        st->breakdown = 1;
+        st->done = 1;
+      } else if (k + 1 >= st->max_iter) {
+        st->done = 1;
+      }
+    }
+  }
 }
 
-// K3: beta = r.r(new) / hist[it]; p = r + beta p; the last block advances the iteration
-template <typename TV>
-__global__ void pupdate_kernel(int64_t n, TV* p, const TV* __restrict__ r, const double* rr_part, int nrr,
-                               double* hist, CgState* st) {
-  if (st->done) return;
-  __shared__ double rrn_s, beta_s;
-  if (threadIdx.x < 32) {
-    const double rrn = warp_sum(rr_part, nrr);
-    if (threadIdx.x == 0) {
-      rrn_s = rrn;
-      beta_s = rrn / hist[st->it];
-    }
+// K3: p = r + beta p (force: run although `done` is up -- the residual-replacement driver completes the
+// iteration whose update raised the flag)
+template <typename T>
+__global__ void pupdate_kernel(int64_t n, T* p, const T* __restrict__ r, const CgState* st, int force = 0) {
+  if (st->done && !force) return;
+  if (st->breakdown) return;
+  using V = typename Vec16<T>::type;
+  constexpr int NV = Vec16<T>::N;
+  const T b = (T)st->beta;
+  const int64_t nv = n / NV;
+  for (int64_t j = gtid(); j < nv; j += gstride()) {
+    V pv = reinterpret_cast<V*>(p)[j];
+    V rv = reinterpret_cast<const V*>(r)[j];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) lane_of<T>(pv, u) = fma(b, lane_of<T>(pv, u), lane_of<T>(rv, u));
+    reinterpret_cast<V*>(p)[j] = pv;
   }
-  __syncthreads();
-  const TV b = (TV)beta_s;
-  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = r[i] + b * p[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const int prev = atomicAdd(&st->arrive, 1);
-    if (prev == (int)gridDim.x - 1) {  // every block has read st->it: advance it
-      __threadfence();
-      st->arrive = 0;
-      const int k = st->it + 1;
-      hist[k] = rrn_s;
-      st->it = k;
-      if (rrn_s <= st->tol2) { st->converged = 1; st->done = 1; }
-      else if (k >= st->max_iter) st->done = 1;
-    }
-  }
+  for (int64_t i = nv * NV + gtid(); i < n; i += gstride()) p[i] = fma(b, p[i], r[i]);
 }
 
 // r = b - q (FP64) with partials of r.r
@@ -221,6 +270,37 @@ __global__ void dot_kernel(int64_t n, const double* __restrict__ a, const double
 // x += scale * d (FP64 update of the refinement)
 __global__ void correct_kernel(int64_t n, double* x, const float* __restrict__ d, double scale) {
   for (int64_t i = gtid(); i < n; i += gstride()) x[i] = fma(scale, (double)d[i], x[i]);
+}
+
+// residual replacement: p32 *= ratio; r32 = r64 * inv_scale (FP32); d32 = 0; partials of r32.r32
+__global__ void replace_kernel(int64_t n, const double* __restrict__ r64, double inv_scale, float ratio, float* r32,
+                               float* p32, float* d32, double* part_a) {
+  double ra = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const float ri = (float)(r64[i] * inv_scale);
+    r32[i] = ri;
+    p32[i] *= ratio;
+    d32[i] = 0.0f;
+    ra = fma((double)ri, (double)ri, ra);
+  }
+  const double s = block_sum(ra);
+  if (threadIdx.x == 0) part_a[blockIdx.x] = s;
+}
+
+// after a replacement: hist[it] = r32.r32, new trigger delta2 * r32.r32, iterations continue
+__global__ void replace_finish_kernel(const double* part_a, int na, double delta2, double* hist, CgState* st) {
+  if (threadIdx.x >= 32) return;
+  const double rr = warp_sum(part_a, na);
+  if (threadIdx.x == 0) {
+    hist[st->it] = rr;
+    st->tol2 = delta2 * rr;
+    st->grow_limit = 1e12 * rr;
+    st->arrive_dot = 0;
+    st->arrive_rr = 0;
+    st->converged = 0;
+    st->breakdown = 0;
+    st->done = st->it >= st->max_iter ? 1 : 0;
+  }
 }
 
 double now_s() {
@@ -253,7 +333,7 @@ ehyb_status_t work_get(ehyb_plan_t P, int hist_need, CgWork** out) {
   const size_t v64 = al((size_t)(n + 2) * 8), v32 = al((size_t)(n + 4) * 4);
   const size_t parts = al((size_t)kVB * 8), pq = al((size_t)(w->nparts + 1) * 8);
   const size_t hist = al((size_t)(w->hist_cap + 2) * 8), st = al(sizeof(CgState));
-  const size_t total = 5 * v64 + 4 * v32 + 2 * parts + pq + hist + st;
+  const size_t total = 6 * v64 + 4 * v32 + 2 * parts + pq + hist + st;
   ehyb_status_t s = device_alloc(&w->arena, total);
   if (s != EHYB_OK) {
     delete w;
@@ -265,6 +345,7 @@ ehyb_status_t work_get(ehyb_plan_t P, int hist_need, CgWork** out) {
   w->r = (double*)b; b += v64;
   w->p = (double*)b; b += v64;
   w->q = (double*)b; b += v64;
+  w->xs = (double*)b; b += v64;
   w->r32 = (float*)b; b += v32;
   w->p32 = (float*)b; b += v32;
   w->q32 = (float*)b; b += v32;
@@ -289,16 +370,15 @@ ehyb_status_t enqueue_chunk(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s) 
   const DevPlan& D = P->dev;
   const int64_t n = D.n;
   for (int k = 0; k < kChunk; ++k) {
+    DotOut dot{w->pq_part, &w->st->arrive_dot, &w->st->pq};
     if (lowp == 0) {
-      CKC(launch_ehyb_f64(D, w->p, w->q, 0, s, w->pq_part, &w->st->done));
-      update_kernel<double, double><<<kVB, kVT, 0, s>>>(n, w->xp, w->p, w->q, w->r, w->pq_part, D.nparts, w->hist,
-                                                        w->st, w->part_a);
-      pupdate_kernel<double><<<kVB, kVT, 0, s>>>(n, w->p, w->r, w->part_a, kVB, w->hist, w->st);
+      CKC(launch_ehyb_f64(D, w->p, w->q, 0, s, &dot, &w->st->done));
+      update_kernel<double><<<kVB, kVT, 0, s>>>(n, w->xp, w->p, w->q, w->r, w->hist, w->st, w->part_a);
+      pupdate_kernel<double><<<kVB, kVT, 0, s>>>(n, w->p, w->r, w->st);
     } else {
-      CKC(launch_ehyb_lowp(D, lowp, w->p32, w->q32, 0, s, w->pq_part, &w->st->done));
-      update_kernel<float, float><<<kVB, kVT, 0, s>>>(n, w->d32, w->p32, w->q32, w->r32, w->pq_part, D.nparts,
-                                                      w->hist, w->st, w->part_a);
-      pupdate_kernel<float><<<kVB, kVT, 0, s>>>(n, w->p32, w->r32, w->part_a, kVB, w->hist, w->st);
+      CKC(launch_ehyb_lowp(D, lowp, w->p32, w->q32, 0, s, &dot, &w->st->done));
+      update_kernel<float><<<kVB, kVT, 0, s>>>(n, w->d32, w->p32, w->q32, w->r32, w->hist, w->st, w->part_a);
+      pupdate_kernel<float><<<kVB, kVT, 0, s>>>(n, w->p32, w->r32, w->st);
     }
     CKC(cudaGetLastError());
   }
@@ -345,7 +425,8 @@ ehyb_status_t sum_parts(CgWork* w, cudaStream_t s, double* out) {
 }
 
 // CG loop on the vectors of w (FP64 or inner FP32); returns iterations and convergence
-ehyb_status_t cg_loop(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s, int* iters, int* converged) {
+ehyb_status_t cg_loop(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s, int* iters, int* converged,
+                      int* breakdown = nullptr) {
   CgState h;
   for (;;) {
     ehyb_status_t st = run_chunk(P, w, lowp, s);
@@ -355,6 +436,7 @@ ehyb_status_t cg_loop(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s, int* i
   }
   *iters = h.it;
   *converged = h.converged;
+  if (breakdown) *breakdown = h.breakdown;
   return EHYB_OK;
 }
 
@@ -369,8 +451,9 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
   if (!P || !info) return EHYB_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));
   if (P->host_only) return EHYB_ERR_UNSUPPORTED;
-  if (refine < 0 || refine > 2 || !(rtol >= 0.0) || max_iter < 0) return EHYB_ERR_INVALID_ARG;
-  if (refine && P->lowp != refine) return EHYB_ERR_UNSUPPORTED;  // the plan lacks that value copy
+  if (refine < 0 || refine > 4 || !(rtol >= 0.0) || max_iter < 0) return EHYB_ERR_INVALID_ARG;
+  const int lowp = refine == 0 ? 0 : (refine == 1 || refine == 3) ? 1 : 2;
+  if (refine && P->lowp != lowp) return EHYB_ERR_UNSUPPORTED;  // the plan lacks that value copy
   if (P->er_layout != 0) return EHYB_ERR_UNSUPPORTED;            // the fused dot needs the sliced ER layout
   const int64_t n = P->dev.n;
   const double t0 = now_s();
@@ -403,6 +486,63 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
     CKC(cudaMemcpyAsync(&rr_last, w->hist + iters, sizeof(double), cudaMemcpyDeviceToHost, s));
     CKC(cudaStreamSynchronize(s));
     info->relres_recursive = std::sqrt(rr_last) / bnorm;
+  } else if (refine >= 3) {
+    // residual replacement: low-precision CG iterations that keep their search direction; whenever the
+    // low-precision residual has dropped by `delta`, x += s d in FP64, the residual is recomputed in FP64
+    // and the iteration continues on it (p rescaled, not restarted)
+    const double delta = inner_rtol > 0.0 ? inner_rtol : 0.1;
+    CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+    residual_kernel<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, w->part_a);
+    double rr = 0.0;
+    if ((st = sum_parts(w, s, &rr)) != EHYB_OK) return st;
+    double scale = std::sqrt(rr);
+    if (scale / bnorm <= rtol || rr == 0.0) {
+      converged = 1;
+    } else {
+      init32_kernel<<<kVB, kVT, 0, s>>>(n, w->r, 1.0 / scale, w->r32, w->p32, w->d32, w->part_a);
+      init_finish_kernel<<<1, 32, 0, s>>>(w->part_a, kVB, nullptr, 0, delta * delta, 1, max_iter, w->hist, w->st);
+      CKC(cudaGetLastError());
+      double prev_rr = rr;
+      int rejections = 0;
+      for (;;) {
+        int it_in = 0, conv_in = 0, brk = 0;
+        if ((st = cg_loop(P, w, lowp, s, &it_in, &conv_in, &brk)) != EHYB_OK) return st;
+        iters = it_in;
+        // the direction update of the iteration that raised the trigger was skipped with it
+        if (conv_in) pupdate_kernel<float><<<kVB, kVT, 0, s>>>(n, w->p32, w->r32, w->st, 1);
+        CKC(cudaMemcpyAsync(w->xs, w->xp, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        correct_kernel<<<kVB, kVT, 0, s>>>(n, w->xp, w->d32, scale);
+        CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+        residual_kernel<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, w->part_a);
+        if ((st = sum_parts(w, s, &rr)) != EHYB_OK) return st;
+        ++outer;
+        bool rejected = false;
+        if (!(rr < prev_rr)) {  // the correction did not help (or is not finite): undo it
+          rejected = true;
+          CKC(cudaMemcpyAsync(w->xp, w->xs, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+          CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+          residual_kernel<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, w->part_a);
+          if ((st = sum_parts(w, s, &rr)) != EHYB_OK) return st;
+        }
+        const double rel = std::sqrt(rr) / bnorm;
+        info->relres_recursive = rel;
+        if (rel <= rtol) { converged = 1; break; }
+        rejections = rejected ? rejections + 1 : 0;
+        if (iters >= max_iter || rr == 0.0 || !std::isfinite(rr) || rejections >= 3) break;
+        const double ns = std::sqrt(rr);
+        if (brk || rejected) {
+          // lost positive definiteness along p, or no progress: restart the direction from the residual
+          init32_kernel<<<kVB, kVT, 0, s>>>(n, w->r, 1.0 / ns, w->r32, w->p32, w->d32, w->part_a);
+        } else {
+          replace_kernel<<<kVB, kVT, 0, s>>>(n, w->r, 1.0 / ns, (float)(scale / ns), w->r32, w->p32, w->d32,
+                                             w->part_a);
+        }
+        replace_finish_kernel<<<1, 32, 0, s>>>(w->part_a, kVB, delta * delta, w->hist, w->st);
+        CKC(cudaGetLastError());
+        scale = ns;
+        prev_rr = rr;
+      }
+    }
   } else {
     // FP64 residual outside, FP32-vector CG on the low-precision values inside
     const double irtol = inner_rtol > 0.0 ? inner_rtol : (refine == 1 ? 1e-4 : 1e-2);
@@ -425,7 +565,7 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
                                           w->st);
       CKC(cudaGetLastError());
       int it_in = 0, conv_in = 0;
-      if ((st = cg_loop(P, w, refine, s, &it_in, &conv_in)) != EHYB_OK) return st;
+      if ((st = cg_loop(P, w, lowp, s, &it_in, &conv_in)) != EHYB_OK) return st;
       iters += it_in;
       correct_kernel<<<kVB, kVT, 0, s>>>(n, w->xp, w->d32, rnorm);
       CKC(cudaGetLastError());

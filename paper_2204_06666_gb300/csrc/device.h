@@ -46,13 +46,19 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 
 // Fused slab + ER kernel.  xp is in the plan numbering; y is written at new_to_old[r] when
 // scatter != 0, else at r.
-// dot_part (optional, sliced ER layout only): per-block partial sums of y_r * xp_r in FP64, fixed order.
+// Fused dot product sum_r y_r * xp_r in FP64 (sliced ER layout only): one partial per partition in
+// part[nparts]; the last block reduces them in a fixed order into *result and resets *arrive (zero).
+struct DotOut {
+  double* part;
+  int32_t* arrive;
+  double* result;
+};
 // skip (optional): device flag; the launch returns at once while it is non-zero.
 cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s,
-                            double* dot_part = nullptr, const int32_t* skip = nullptr);
+                            const DotOut* dot = nullptr, const int32_t* skip = nullptr);
 // values stored FP32 (lowp = 1) or BF16 (lowp = 2); x, y and the accumulation in FP32
 cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s,
-                             double* dot_part = nullptr, const int32_t* skip = nullptr);
+                             const DotOut* dot = nullptr, const int32_t* skip = nullptr);
 
 // plain vector-CSR baseline: tpr lanes per row
 cudaError_t launch_csr_f64(int64_t n, const int64_t* rp, const int32_t* col, const double* val, const double* x,

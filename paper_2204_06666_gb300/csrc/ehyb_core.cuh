@@ -107,7 +107,9 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(
 
 constexpr int kBatch = 8;  // slots whose loads are issued before their FMAs
 
-// acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory
+// acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory.  Loads are issued
+// kBatch at a time ahead of their FMAs; the FMAs run in slot order.  (A predicated last batch measured
+// slower than this scalar remainder on both 3D workloads.)
 template <typename V, typename X>
 __device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
                                       const X* xs, X acc) {
@@ -169,8 +171,20 @@ struct KArgs {
   uint64_t timeout_ns;
   int32_t inject;
   double* dot_part;       // optional: per-block partial of sum_r y_r * xp_r (fixed summation order)
+  int32_t* dot_arrive;    // optional (with dot_part, one block per partition): arrival counter; the last
+  double* dot_result;     //   block reduces the partials into *dot_result and resets the counter
   const int32_t* skip;    // optional: the launch does nothing while *skip != 0 (converged solver)
 };
+
+// warp-level fixed-order sum of count values (lane-strided, then an xor tree); every lane gets it
+__device__ __forceinline__ double warp_sum_fixed(const double* part, int count) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+#pragma unroll 4
+  for (int i = lane; i < count; i += 32) v += part[i];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+  return v;
+}
 
 // Deterministic block sum (xor-tree inside warps, warps in index order); result in thread 0.
 __device__ __forceinline__ double block_sum_fixed(double v, double* ws) {
@@ -192,12 +206,13 @@ struct BlockState {
   int bar_ready;       // bar has been initialised
   int slice_counter;   // next slice of the current partition
   int stage_ok;
+  int is_last;
   double ws[32];
 };
 
 // One partition p of a plan: stage its slice of x_p, run its slab (and ER) slices, write y.
 // Returns false (uniformly across the block) when the staging wait ran out of time.
-template <typename V, typename X, bool SCATTER, bool ER_SLICED>
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false>
 __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
                                                const V* __restrict__ er_val, const X* __restrict__ xp,
                                                X* __restrict__ y, const int p, X* xs, BlockState& bs) {
@@ -260,18 +275,41 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
 
   // ---- 2. slab: warp per 32-lane slice, dynamic slice balancing inside the partition
   // (static round-robin when the fused dot product is requested, so its order is fixed)
-  const bool dot = a.dot_part != nullptr;
+  constexpr bool dot = DOT;  // a.dot_part is set
   double dacc = 0.0;
   int s = s0 + warp;
-  while (s < s1) {
-    const int64_t pos = a.slice_pos[s];
-    const int w = (int)((a.slice_pos[s + 1] - pos) >> 5);
-    X acc = slab_dot<V, X>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
+  int64_t pos = 0, epos = 0;
+  int w = 0, we = 0;
+  if (s < s1) {
+    pos = a.slice_pos[s];
+    w = (int)((a.slice_pos[s + 1] - pos) >> 5);
     if (ER_SLICED) {
-      const int64_t epos = a.er_slice_pos[s];
-      const int we = (int)((a.er_slice_pos[s + 1] - epos) >> 5);
-      acc = er_dot<V, X>(er_val + epos + lane, a.er_scol + epos + lane, we, xp, acc);
+      epos = a.er_slice_pos[s];
+      we = (int)((a.er_slice_pos[s + 1] - epos) >> 5);
     }
+  }
+  while (s < s1) {
+    // reserve the next slice and start its metadata loads before working on this one
+    int nxt;
+    if (dot) {
+      nxt = s + nwarps;
+    } else {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(&bs.slice_counter, 1);
+      nxt = __shfl_sync(FULL, t, 0);
+    }
+    int64_t npos = 0, nepos = 0;
+    int nw = 0, nwe = 0;
+    if (nxt < s1) {
+      npos = a.slice_pos[nxt];
+      nw = (int)((a.slice_pos[nxt + 1] - npos) >> 5);
+      if (ER_SLICED) {
+        nepos = a.er_slice_pos[nxt];
+        nwe = (int)((a.er_slice_pos[nxt + 1] - nepos) >> 5);
+      }
+    }
+    X acc = slab_dot<V, X>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
+    if (ER_SLICED) acc = er_dot<V, X>(er_val + epos + lane, a.er_scol + epos + lane, we, xp, acc);
     for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
     if (sub == 0 && row < pe) {
@@ -279,17 +317,30 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       else y[row] = acc;
       if (dot) dacc = fma((double)acc, (double)xsl[row - pb], dacc);
     }
-    if (dot) {
-      s += nwarps;
-    } else {
-      int nxt = 0;
-      if (lane == 0) nxt = atomicAdd(&bs.slice_counter, 1);
-      s = __shfl_sync(FULL, nxt, 0);
-    }
+    s = nxt;
+    pos = npos;
+    w = nw;
+    epos = nepos;
+    we = nwe;
   }
   if (dot) {  // only offered for the sliced ER layout, where a slice's rows are final here
     const double t = block_sum_fixed(dacc, bs.ws);
     if (tid == 0) a.dot_part[p] = t;
+    if (a.dot_arrive) {
+      if (tid == 0) {
+        __threadfence();
+        bs.is_last = atomicAdd(a.dot_arrive, 1) == (int)gridDim.x - 1;
+      }
+      __syncthreads();
+      if (bs.is_last && tid < 32) {
+        __threadfence();
+        const double sum = warp_sum_fixed(a.dot_part, (int)gridDim.x);
+        if (tid == 0) {
+          *a.dot_result = sum;
+          *a.dot_arrive = 0;
+        }
+      }
+    }
   }
   if (ER_SLICED) return true;
   const int e0 = a.er_part_ptr[p];
@@ -358,6 +409,8 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.timeout_ns = P.wait_timeout_ns;
   a.inject = P.inject_wait_fault;
   a.dot_part = nullptr;
+  a.dot_arrive = nullptr;
+  a.dot_result = nullptr;
   a.skip = nullptr;
   return a;
 }

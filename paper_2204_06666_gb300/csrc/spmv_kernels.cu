@@ -11,7 +11,7 @@ namespace {
 
 using namespace core;
 
-template <typename V, typename X, bool SCATTER, bool ER_SLICED>
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT>
 __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
                                                     const V* __restrict__ er_val, const X* __restrict__ xp,
                                                     X* __restrict__ y) {
@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     bs.bar_ready = 0;
     bs.phase = 0;
   }
-  partition_spmv<V, X, SCATTER, ER_SLICED>(a, ell_val, er_val, xp, y, blockIdx.x, reinterpret_cast<X*>(smem_raw), bs);
+  partition_spmv<V, X, SCATTER, ER_SLICED, DOT>(a, ell_val, er_val, xp, y, blockIdx.x,
+                                                reinterpret_cast<X*>(smem_raw), bs);
 }
 
 template <typename X>
@@ -68,13 +69,12 @@ size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes) {
 template <typename V, typename X>
 static cudaError_t set_smem(int bytes) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-    return e;
-  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-    return e;
-  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-    return e;
-  return cudaFuncSetAttribute(ehyb_kernel<V, X, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false>, attr, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false, false>, attr, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false>, attr, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, false, false>, attr, bytes))) return e;
+  return cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true>, attr, bytes);
 }
 
 cudaError_t kernels_init(int smem_optin) {
@@ -98,37 +98,43 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 
 template <typename V, typename X>
 static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const V* erv_sl, const X* xp, X* y,
-                         int scatter, size_t smem, cudaStream_t s, double* dot_part, const int32_t* skip) {
+                         int scatter, size_t smem, cudaStream_t s, const DotOut* dot, const int32_t* skip) {
   KArgs a = make_kargs(P);
-  a.dot_part = dot_part;
+  if (dot) {
+    a.dot_part = dot->part;
+    a.dot_arrive = dot->arrive;
+    a.dot_result = dot->result;
+  }
   a.skip = skip;
   const bool sl = P.er_layout == 0;
   const V* erv = sl ? erv_sl : erv_csr;
-  if (scatter) {
-    if (sl) ehyb_kernel<V, X, true, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
-    else ehyb_kernel<V, X, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+  if (dot) {  // the fused dot product exists for the sliced layout in the plan numbering (solver use)
+    ehyb_kernel<V, X, false, true, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+  } else if (scatter) {
+    if (sl) ehyb_kernel<V, X, true, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    else ehyb_kernel<V, X, true, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
   } else {
-    if (sl) ehyb_kernel<V, X, false, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
-    else ehyb_kernel<V, X, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    if (sl) ehyb_kernel<V, X, false, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    else ehyb_kernel<V, X, false, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
   }
 }
 
 cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s,
-                            double* dot_part, const int32_t* skip) {
+                            const DotOut* dot, const int32_t* skip) {
   if (P.nparts == 0) return cudaSuccess;
-  launch_typed<double, double>(P, P.ell_val, P.er_val, P.er_sval, xp, y, scatter, ehyb_smem_bytes(P, 8), s, dot_part,
+  launch_typed<double, double>(P, P.ell_val, P.er_val, P.er_sval, xp, y, scatter, ehyb_smem_bytes(P, 8), s, dot,
                                skip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ehyb_lowp(const DevPlan& P, int lowp, const float* xp, float* y, int scatter, cudaStream_t s,
-                             double* dot_part, const int32_t* skip) {
+                             const DotOut* dot, const int32_t* skip) {
   if (P.nparts == 0) return cudaSuccess;
   const size_t smem = ehyb_smem_bytes(P, 4);
   if (lowp == 1)
-    launch_typed<float, float>(P, P.ell_val_f32, P.er_val_f32, P.er_sval_f32, xp, y, scatter, smem, s, dot_part, skip);
+    launch_typed<float, float>(P, P.ell_val_f32, P.er_val_f32, P.er_sval_f32, xp, y, scatter, smem, s, dot, skip);
   else
-    launch_typed<uint16_t, float>(P, P.ell_val_bf16, P.er_val_bf16, P.er_sval_bf16, xp, y, scatter, smem, s, dot_part,
+    launch_typed<uint16_t, float>(P, P.ell_val_bf16, P.er_val_bf16, P.er_sval_bf16, xp, y, scatter, smem, s, dot,
                                   skip);
   return cudaGetLastError();
 }

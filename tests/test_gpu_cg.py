@@ -113,7 +113,7 @@ def test_cg_not_converged_status(eh):
     assert st == 0 and info["iterations"] == 0 and np.all(x == 0)
 
 
-@pytest.mark.parametrize("refine,lowp", [(1, 1), (2, 2)])
+@pytest.mark.parametrize("refine,lowp", [(1, 1), (2, 2), (3, 1), (4, 2)])
 def test_refined_cg_reaches_fp64_accuracy(eh, refine, lowp):
     A = gen.tet_lap3d(N=24)
     xstar = gen.uniform(A.n, 23)
