@@ -227,3 +227,66 @@ def fem_batch(count: int = 64, seed: int = 31, n_min: int = 5000, n_max: int = 3
             A = hex_elast3d(N=max(2, int(round((n / 3) ** (1 / 3)))), seed_mesh=s_mesh, seed_perm=s_perm)
         out.append(A)
     return out
+
+
+def powerlaw_csr(n: int, seed: int, alpha: float, min_len: int = 2, max_len: int = 5000, local_frac: float = 0.7,
+                 symmetric: bool = True) -> CSR:
+    """Random sparse matrix with power-law row lengths, to stress the extra-row tail.
+
+    Row lengths follow P(k) ~ k^-alpha on [min_len, max_len]; 70 % of each row's columns fall in a window of
+    +-max(32, k) around the row in a hidden order (locality a partitioner can find), 30 % are uniform.  The
+    pattern is symmetrised and given a diagonal; values are symmetric U[-1, 1) off the diagonal and the
+    diagonal is 1 + the row's absolute off-diagonal sum (so the matrix is SPD).  The row order is random.
+    """
+    rng = np.random.default_rng(seed)
+    ks = np.arange(min_len, max_len + 1, dtype=np.float64)
+    pk = ks ** (-alpha)
+    lens = rng.choice(np.arange(min_len, max_len + 1), size=n, p=pk / pk.sum())
+    hidden = rng.permutation(n)            # hidden[pos] = row at that position
+    pos = np.empty(n, np.int64)
+    pos[hidden] = np.arange(n)
+    rows = np.repeat(np.arange(n, dtype=np.int64), lens)
+    total = rows.size
+    win = np.maximum(32, lens)[rows]
+    off = np.floor((rng.random(total) * 2.0 - 1.0) * (win + 1)).astype(np.int64)
+    loc_cols = hidden[np.clip(pos[rows] + off, 0, n - 1)]
+    cols = np.where(rng.random(total) < local_frac, loc_cols, rng.integers(0, n, total))
+    if symmetric:
+        rows, cols = np.concatenate([rows, cols]), np.concatenate([cols, rows])
+    key = np.unique(rows * n + cols)
+    r, c = key // n, key % n
+    off_mask = r != c
+    r, c = r[off_mask], c[off_mask]
+    lo, hi = np.minimum(r, c), np.maximum(r, c)
+    with np.errstate(over="ignore"):
+        h = (lo.astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15) + hi.astype(np.uint64) * np.uint64(0xBF58476D1CE4E5B9)
+             + np.uint64(seed)) >> np.uint64(11)
+    v = (h.astype(np.float64) / float(1 << 53)) * 2.0 - 1.0   # symmetric value per unordered pair
+    diag = np.bincount(r, weights=np.abs(v), minlength=n) + 1.0
+    r = np.concatenate([r, np.arange(n)])
+    c = np.concatenate([c, np.arange(n)])
+    v = np.concatenate([v, diag])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, r + 1, 1)
+    return CSR(n, np.cumsum(rp), c.astype(np.int32), v, f"powerlaw_n{n}_a{alpha:.2f}")
+
+
+def tuner_matrix(index: int, base_seed: int = 1000, n_min: int = 5000, n_max: int = 100000) -> CSR:
+    """Matrix number `index` of the tuner's data set: even indices are FEM-like (the four element kinds of
+    fem_batch), odd ones power-law (alpha ~ U[2, 3]); rows log-uniform in [n_min, n_max]; seed base + index."""
+    seed = base_seed + index
+    rng = np.random.default_rng(seed)
+    n = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+    if index % 2 == 1:
+        return powerlaw_csr(int(n), seed, float(rng.uniform(2.0, 3.0)))
+    kind = BATCH_KINDS[int(rng.integers(0, 4))]
+    sm, sp = 2 * seed + 1, 2 * seed + 2
+    if kind == "fem2d_p1":
+        return fem2d_p1(N=max(2, int(round(n ** 0.5))), seed_mesh=sm, seed_perm=sp)
+    if kind == "tet_lap3d":
+        return tet_lap3d(N=max(2, int(round(n ** (1 / 3)))), seed_mesh=sm, seed_perm=sp, dirichlet=False)
+    if kind == "hex_lap3d":
+        return hex_lap3d(N=max(2, int(round(n ** (1 / 3)))), seed_mesh=sm, seed_perm=sp)
+    return hex_elast3d(N=max(2, int(round((n / 3) ** (1 / 3)))), seed_mesh=sm, seed_perm=sp)

@@ -80,6 +80,9 @@ typedef struct {
                                 1 = CSR lines, er_tpr lanes each with a shuffle reduction, after a block barrier */
   int32_t part_nnz;          /* when slice_rows is 0: size partitions for about this many entries each (capped by
                                 shared memory) instead of Eq. 1's one-per-SM split; for plans run in a batch */
+  int32_t tuner;             /* knob choice when slice_rows, ell_width_cap and ell_tpr are 0: 0 = Eq. 1 default,
+                                1 = learned model (ehyb_tuner_set_model) with the sweep as fallback when the plan
+                                runs over 2x the model's predicted time, 2 = exhaustive sweep (ehyb_tune_sweep) */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;
@@ -98,6 +101,9 @@ typedef struct {
   int32_t num_sms;
   int32_t er_layout;         /* as ehyb_options_t.er_layout */
   int64_t er_stored;         /* sliced layout: ER slots including padding (CSR layout: er_nnz) */
+  int32_t tuner_path;        /* 0 options as given, 1 learned choice kept, 2 sweep, 3 learned choice failed its
+                                sanity check and the sweep decided */
+  int32_t ell_width_cap;     /* slab width cap in force (0 = none) */
 } ehyb_plan_info_t;
 
 /* Pointers into arrays owned by the plan (valid until ehyb_destroy); see ehyb_plan_export. */
@@ -280,6 +286,63 @@ ehyb_status_t ehyb_csr_create(int64_t n, int64_t nnz, const int64_t* row_ptr, co
 ehyb_status_t ehyb_csr_spmv(ehyb_csr_t m, const double* x, double* y, void* stream);
 ehyb_status_t ehyb_csr_set_tpr(ehyb_csr_t m, int32_t tpr);
 ehyb_status_t ehyb_csr_destroy(ehyb_csr_t m);
+
+/* ---- knob tuning (not in the paper: Eq. 1 fixes VecSize; this chooses VecSize, the slab width cap and
+ *      the lanes per row per matrix) ---- */
+
+typedef struct {
+  int32_t slice_rows, ell_width_cap, ell_tpr, valid;
+  double ms;                 /* measured ehyb_spmv time (sweep), 0 when not timed */
+} ehyb_tune_entry_t;
+
+/* Number of knob configurations in the tuning grid (63): VecSize in {Eq. 1 default, 1024, 2048, 4096,
+ * 8192, 16384, shared-memory maximum} x slab width cap in {none, p99, p90 row length} x lanes {1, 2, 4};
+ * entry g has VecSize index g / 9, cap index (g / 3) % 3, lanes index g % 3. */
+int32_t ehyb_tune_grid_size(void);
+
+/* The grid's knob values for this matrix (no GPU use).  table: ehyb_tune_grid_size() entries. */
+ehyb_status_t ehyb_tune_grid(int64_t n, const int64_t* row_ptr, int32_t num_sms, int32_t smem_optin,
+                             ehyb_tune_entry_t* table);
+
+/* 16 features of a host CSR matrix (the tuner's input): log2 n, log2 nnz, mean / std / log2 max / min /
+ * p50 / p90 / p99 row length, share of rows longer than 32, Gini of the row lengths, mean |i-j|/n, share of
+ * entries within n/P of the diagonal, share of diagonally dominant rows, pattern symmetry on up to 1000
+ * sampled rows, share of entries inside contiguous blocks of n/P rows (P = num_sms, 0 = 152). */
+ehyb_status_t ehyb_features(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                            int32_t num_sms, float* out16);
+
+/* Exhaustive sweep: build every grid configuration (host encodings in parallel threads), time its
+ * ehyb_spmv on the current device (two warm-up calls, then the mean of reps, 0 = 10), fill table and
+ * *best (index of the fastest).  Synchronous. */
+ehyb_status_t ehyb_tune_sweep(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const double* val,
+                              int32_t reps, ehyb_tune_entry_t* table, int32_t* best, void* stream);
+
+/* Load the tuner network (host arrays): params = ehyb_mlp_param_count() floats; feature and output
+ * normalisation (x_norm = (x - mean) / std; outputs = net * out_std + out_mean).  params NULL unloads. */
+ehyb_status_t ehyb_tuner_set_model(const float* params, const float* feat_mean, const float* feat_std,
+                                   const float* out_mean, const float* out_std);
+
+/* The loaded model's knob choice for a matrix and its predicted ehyb_spmv time per entry (ns). */
+ehyb_status_t ehyb_tuner_predict(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                                 const double* val, int32_t* slice_rows, int32_t* ell_width_cap, int32_t* ell_tpr,
+                                 double* pred_ns_per_nnz);
+
+/* ---- the tuner network's kernels: MLP 16 -> 64 -> 64 -> 4, ReLU, FP32, MSE loss, Adam ---- */
+
+int32_t ehyb_mlp_param_count(void);                /* 5508 */
+int64_t ehyb_mlp_workspace_bytes(int32_t batch);   /* device workspace for a batch */
+
+/* out (batch x 4) = net(X (batch x 16)); all device arrays, row-major.  Asynchronous on `stream`. */
+ehyb_status_t ehyb_mlp_forward(const float* params, const float* X, int32_t batch, float* out, void* workspace,
+                               void* stream);
+
+/* loss = mean((net(X) - T)^2) over batch x 4 outputs, grad = dloss/dparams (device arrays). */
+ehyb_status_t ehyb_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t batch, float* grad,
+                                 float* loss, void* workspace, void* stream);
+
+/* One Adam step (Kingma & Ba) with bias correction for step number `step` >= 1, on device arrays. */
+ehyb_status_t ehyb_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t step, float lr,
+                            float beta1, float beta2, float eps, void* stream);
 
 /* ---- test hook (host-side fault injection) ---- */
 

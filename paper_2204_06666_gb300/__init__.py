@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("smem_budget", ctypes.c_int32),
                 ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
                 ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32)]
+                ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32), ("tuner", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -55,7 +55,8 @@ class PlanInfo(ctypes.Structure):
                 ("er_rows", ctypes.c_int64), ("er_nnz", ctypes.c_int64), ("bytes_effective", ctypes.c_int64),
                 ("bytes_device", ctypes.c_int64), ("partition_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
                 ("upload_ms", ctypes.c_double), ("device_status", ctypes.c_int32), ("num_sms", ctypes.c_int32),
-                ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64)]
+                ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64), ("tuner_path", ctypes.c_int32),
+                ("ell_width_cap", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +79,11 @@ class CgInfo(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("slice_rows", ctypes.c_int32), ("ell_width_cap", ctypes.c_int32), ("ell_tpr", ctypes.c_int32),
+                ("valid", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 _P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -109,6 +115,18 @@ _sig("ehyb_batch_create", [_I32, _P, ctypes.POINTER(_P)])
 _sig("ehyb_batch_spmv", [_P, _P, _P, _P])
 _sig("ehyb_batch_info", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _sig("ehyb_batch_destroy", [_P])
+_sig("ehyb_tune_grid_size", [], _I32)
+_sig("ehyb_tune_grid", [_I64, _P, _I32, _I32, _P])
+_sig("ehyb_features", [_I64, _P, _P, _P, _I32, _P])
+_sig("ehyb_tune_sweep", [_I64, _I64, _P, _P, _P, _I32, _P, ctypes.POINTER(_I32), _P])
+_sig("ehyb_tuner_set_model", [_P, _P, _P, _P, _P])
+_sig("ehyb_tuner_predict", [_I64, _I64, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                            ctypes.POINTER(_I32), ctypes.POINTER(_D)])
+_sig("ehyb_mlp_param_count", [], _I32)
+_sig("ehyb_mlp_workspace_bytes", [_I32], _I64)
+_sig("ehyb_mlp_forward", [_P, _P, _I32, _P, _P, _P])
+_sig("ehyb_mlp_loss_grad", [_P, _P, _P, _I32, _P, _P, _P, _P])
+_sig("ehyb_mlp_adam", [_P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P])
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
@@ -403,3 +421,107 @@ class Batch:
                 _lib.ehyb_batch_destroy(self._h)
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- tuner
+
+def _csr_arrays(A):
+    rp = np.ascontiguousarray(A.row_ptr, np.int64)
+    c = np.ascontiguousarray(A.col, np.int32)
+    v = np.ascontiguousarray(A.val, np.float64)
+    return rp, c, v
+
+
+def features(A, num_sms: int = 152) -> np.ndarray:
+    """The tuner's 16 matrix features (ehyb_features)."""
+    rp, c, v = _csr_arrays(A)
+    out = np.zeros(16, np.float32)
+    _check(_lib.ehyb_features(int(A.n), rp.ctypes.data, c.ctypes.data, v.ctypes.data, num_sms, out.ctypes.data),
+           "ehyb_features")
+    return out
+
+
+def _table_dicts(tab):
+    return [{"slice_rows": e.slice_rows, "ell_width_cap": e.ell_width_cap, "ell_tpr": e.ell_tpr,
+             "valid": bool(e.valid), "ms": e.ms} for e in tab]
+
+
+def tune_grid(A, num_sms: int = 152, smem_optin: int = 232448):
+    """The knob configurations of the tuning grid for this matrix (no GPU use)."""
+    g = _lib.ehyb_tune_grid_size()
+    tab = (TuneEntry * g)()
+    rp = np.ascontiguousarray(A.row_ptr, np.int64)
+    _check(_lib.ehyb_tune_grid(int(A.n), rp.ctypes.data, num_sms, smem_optin, tab), "ehyb_tune_grid")
+    return _table_dicts(tab)
+
+
+def tune_sweep(A, reps: int = 10, stream=None):
+    """Exhaustive sweep: (table of configurations with measured ms, index of the fastest)."""
+    g = _lib.ehyb_tune_grid_size()
+    tab = (TuneEntry * g)()
+    best = ctypes.c_int32(-1)
+    rp, c, v = _csr_arrays(A)
+    _check(_lib.ehyb_tune_sweep(int(A.n), int(rp[-1]), rp.ctypes.data, c.ctypes.data, v.ctypes.data, reps, tab,
+                                ctypes.byref(best), _stream(stream)), "ehyb_tune_sweep")
+    return _table_dicts(tab), best.value
+
+
+def tuner_set_model(params, feat_mean, feat_std, out_mean, out_std):
+    """Load the tuner network (numpy float32 arrays) into the library; params=None unloads it."""
+    if params is None:
+        _check(_lib.ehyb_tuner_set_model(None, None, None, None, None), "ehyb_tuner_set_model")
+        return
+    arrs = [np.ascontiguousarray(a, np.float32) for a in (params, feat_mean, feat_std, out_mean, out_std)]
+    _check(_lib.ehyb_tuner_set_model(*[a.ctypes.data for a in arrs]), "ehyb_tuner_set_model")
+
+
+def tuner_predict(A):
+    """(slice_rows, ell_width_cap, ell_tpr, predicted ns per entry) from the loaded model."""
+    rp, c, v = _csr_arrays(A)
+    sr, cap, tpr, ns = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+    _check(_lib.ehyb_tuner_predict(int(A.n), int(rp[-1]), rp.ctypes.data, c.ctypes.data, v.ctypes.data,
+                                   ctypes.byref(sr), ctypes.byref(cap), ctypes.byref(tpr), ctypes.byref(ns)),
+           "ehyb_tuner_predict")
+    return sr.value, cap.value, tpr.value, ns.value
+
+
+class Mlp:
+    """Device-side training state of the tuner network, driven through the library's MLP kernels.
+    All tensors are torch float32 CUDA tensors."""
+
+    def __init__(self, params):
+        import torch
+        self.n = int(_lib.ehyb_mlp_param_count())
+        self.params = params.to(device="cuda", dtype=torch.float32).contiguous().clone()
+        assert self.params.numel() == self.n
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.step_no = 0
+        self._ws = None
+
+    def _workspace(self, batch):
+        import torch
+        need = int(_lib.ehyb_mlp_workspace_bytes(batch))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 4), dtype=torch.uint8, device="cuda")
+        return self._ws.data_ptr()
+
+    def forward(self, X):
+        import torch
+        out = torch.empty((X.shape[0], 4), dtype=torch.float32, device="cuda")
+        _check(_lib.ehyb_mlp_forward(self.params.data_ptr(), _dev(X, "float32"), X.shape[0], out.data_ptr(),
+                                     self._workspace(X.shape[0]), _stream(None)), "ehyb_mlp_forward")
+        return out
+
+    def loss_grad(self, X, T):
+        _check(_lib.ehyb_mlp_loss_grad(self.params.data_ptr(), _dev(X, "float32"), _dev(T, "float32"), X.shape[0],
+                                       self.grad.data_ptr(), self.loss.data_ptr(), self._workspace(X.shape[0]),
+                                       _stream(None)), "ehyb_mlp_loss_grad")
+        return self.loss, self.grad
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step_no += 1
+        _check(_lib.ehyb_mlp_adam(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr(),
+                                  self.step_no, lr, beta1, beta2, eps, _stream(None)), "ehyb_mlp_adam")

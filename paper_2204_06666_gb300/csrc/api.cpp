@@ -126,6 +126,15 @@ struct ehyb_csr_s {
 
 namespace ehyb {
 ehyb_status_t cuda_error_status(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+ehyb_status_t device_query(int* dev, int* sms, int* smem_optin) {
+  DeviceInfo d;
+  ehyb_status_t st = query_device(d);
+  if (st != EHYB_OK) return st;
+  *dev = d.dev;
+  *sms = d.sms;
+  *smem_optin = d.smem_optin;
+  return EHYB_OK;
+}
 ehyb_status_t device_alloc(void** p, size_t bytes) { return dev_alloc(p, bytes); }
 
 // device view of a plan for entry points defined in other translation units
@@ -202,6 +211,38 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   }
   const int64_t budget = opt.smem_budget > 0 ? opt.smem_budget : (int64_t)d.smem_optin - 1024;
   if (opt.num_sms > 0) d.sms = opt.num_sms;
+  if (opt.tuner < 0 || opt.tuner > 2) return EHYB_ERR_INVALID_ARG;
+  const bool knobs_free = opt.slice_rows == 0 && opt.ell_width_cap == 0 && opt.ell_tpr == 1 && !opt.part_vec &&
+                          opt.part_nnz == 0 && opt.er_layout == 0;
+  int32_t tuner_path = 0;
+  double pred_ns = 0.0;
+  if (opt.tuner && knobs_free && !opt.host_only && n > 0) {
+    if (opt.tuner == 1) {
+      int32_t sr = 0, cap = 0, tpr = 1;
+      st = learned_choice(n, row_ptr, col, val, d.sms, d.smem_optin, &sr, &cap, &tpr, &pred_ns);
+      if (st == EHYB_OK) {
+        opt.slice_rows = sr;
+        opt.ell_width_cap = cap;
+        opt.ell_tpr = tpr;
+        tuner_path = 1;
+      } else if (st != EHYB_ERR_UNSUPPORTED) {
+        return st;
+      }
+    }
+    if (tuner_path == 0) {  // the sweep decides (asked for, or no model loaded)
+      ehyb_tune_entry_t table[64];
+      int32_t best = -1;
+      ehyb_plan_t bp = nullptr;
+      ehyb_options_t base = opt;
+      base.tuner = 0;
+      st = sweep_impl(n, row_ptr, col, val, base, 10, table, &best, &bp, stream);
+      if (st != EHYB_OK) return st;
+      bp->tuner_path = 2;
+      bp->ell_width_cap = table[best].ell_width_cap;
+      *out = bp;
+      return EHYB_OK;
+    }
+  }
 
   std::unique_ptr<ehyb_plan_s> P;
   try {
@@ -233,10 +274,49 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   // every partition's slice of x (FP64, plus 16-byte alignment slack) must fit one block's dynamic shared memory
   if ((int64_t)(H.max_part_rows + 2) * 8 > (int64_t)d.smem_optin - 1024) return EHYB_ERR_TOO_LARGE;
 
+  st = plan_finalize(P, opt, d.dev, d.sms, stream, out);
+  if (st != EHYB_OK) return st;
+  (*out)->tuner_path = tuner_path;
+  (*out)->ell_width_cap = opt.ell_width_cap;
+  if (tuner_path == 1) {  // sanity gate: the learned choice must run within 2x of its own prediction
+    double ms = 0.0;
+    st = measure_plan_ms(*out, 5, stream, &ms);
+    if (st != EHYB_OK) return st;
+    const double ns_per_nnz = nnz > 0 ? ms * 1e6 / (double)nnz : 0.0;
+    if (ns_per_nnz > 2.0 * pred_ns) {
+      ehyb_destroy(*out);
+      *out = nullptr;
+      ehyb_tune_entry_t table[64];
+      int32_t best = -1;
+      ehyb_options_t base = opt;
+      base.tuner = 0;
+      base.slice_rows = 0;
+      base.ell_width_cap = 0;
+      base.ell_tpr = 1;
+      st = sweep_impl(n, row_ptr, col, val, base, 10, table, &best, out, stream);
+      if (st != EHYB_OK) return st;
+      (*out)->tuner_path = 3;
+      (*out)->ell_width_cap = table[best].ell_width_cap;
+    }
+  }
+  return EHYB_OK;
+}
+}  // extern "C"
+
+namespace ehyb {
+
+// Everything after the host build: metadata, launch defaults, device upload, dropping bulky host arrays.
+ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_t& opt_in, int dev, int sms,
+                            void* stream, ehyb_plan_t* out) {
+  ehyb_options_t opt = opt_in;
+  HostPlan& H = P->host;
+  const int64_t n = H.n;
+  struct { int dev, sms; } d{dev, sms};
+  ehyb_status_t st = EHYB_OK;
   P->host_only = opt.host_only != 0;
   P->lowp = opt.lowp;
   P->num_sms = d.sms;
-  P->slice_rows = prm.slice_rows;
+  P->slice_rows = H.slice_rows;
   P->ell_nnz = H.ell_nnz;
   P->ell_stored = (int64_t)H.ell_col.size();
   P->er_rows = 0;
@@ -364,6 +444,10 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   *out = P.release();
   return EHYB_OK;
 }
+
+}  // namespace ehyb
+
+extern "C" {
 
 ehyb_status_t ehyb_destroy(ehyb_plan_t p) {
   if (!p) return EHYB_OK;
@@ -508,6 +592,8 @@ ehyb_status_t ehyb_plan_info(ehyb_plan_t p, ehyb_plan_info_t* info) {
   info->bytes_effective = p->ell_nnz * 10 + p->er_nnz * 12 + (p->er_layout == 1 ? p->er_rows * 8 : 0) + H.n * 16;
   info->er_layout = p->er_layout;
   info->er_stored = p->er_stored;
+  info->tuner_path = p->tuner_path;
+  info->ell_width_cap = p->ell_width_cap;
   info->bytes_device = (int64_t)p->arena_bytes;
   info->partition_ms = H.partition_ms;
   info->reorder_ms = H.reorder_ms;

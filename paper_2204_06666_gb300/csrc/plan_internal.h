@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <utility>
 #include <vector>
 
@@ -49,5 +50,24 @@ struct ehyb_plan_s {
   // SpMM workspace: X gathered into the chunk-major plan numbering (allocated by ehyb_spmm)
   void* spmm_ws = nullptr;
   size_t spmm_ws_bytes = 0;
+  int32_t tuner_path = 0;
+  int32_t ell_width_cap = 0;
 };
 
+
+namespace ehyb {
+// Metadata, launch defaults, device upload (unless host-only) of a plan whose host part P->host is built;
+// on success *out owns the plan.
+ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_t& opt, int dev, int sms,
+                            void* stream, ehyb_plan_t* out);
+// SM count, opt-in shared memory per block and current device; initialises the kernels' attributes once
+ehyb_status_t device_query(int* dev, int* sms, int* smem_optin);
+// tuner.cpp: the exhaustive sweep (best plan kept when best_plan is not NULL) and the learned choice
+ehyb_status_t sweep_impl(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                         const ehyb_options_t& base, int reps, ehyb_tune_entry_t* table, int32_t* best_idx,
+                         ehyb_plan_t* best_plan, void* stream);
+ehyb_status_t learned_choice(int64_t n, const int64_t* rp, const int32_t* col, const double* val, int sms,
+                             int smem_optin, int32_t* slice_rows, int32_t* cap, int32_t* tpr, double* pred_ns);
+// mean time of reps ehyb_spmv calls on the plan (allocates its own x and y)
+ehyb_status_t measure_plan_ms(ehyb_plan_t P, int reps, void* stream, double* ms);
+}  // namespace ehyb

@@ -1,0 +1,178 @@
+"""Training and evaluation of the knob tuner (the learned subsystem built around EHYB).
+
+    python -m paper_2204_06666_gb300.tune sweep --start 0 --count 500 --out sweeps_0.npz
+    python -m paper_2204_06666_gb300.tune train --data sweeps_*.npz --out tuner_model.npz
+    python -m paper_2204_06666_gb300.tune evaluate --model tuner_model.npz --data heldout.npz
+
+* sweep: matrix i of the data set (gen.tuner_matrix(i): FEM-like for even i, power-law for odd i, 5k-100k
+  rows) is swept over the 63-configuration grid with ehyb_tune_sweep; features (ehyb_features), the grid
+  and the measured times are stored.
+* train: targets are the fastest configuration's (log2 VecSize, cap index, log2 lanes, log ns per entry),
+  standardised; the 16 -> 64 -> 64 -> 4 network is trained on the GPU by the library's own forward,
+  backward and Adam kernels (Mlp); inputs standardised with the training-set mean and deviation.
+* evaluate: the model is loaded into the library and ehyb_tuner_predict chooses knobs for each held-out
+  matrix; the chosen configuration's swept time over the best swept time is the tuner's ratio (geometric
+  mean, p90, max), compared with the Eq. 1 default configuration's ratio.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+_ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if _ROOT not in sys.path:
+    sys.path.insert(0, _ROOT)
+
+import gen  # noqa: E402
+
+from . import Mlp, features, tune_sweep, tuner_predict, tuner_set_model  # noqa: E402
+
+MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuner_model.npz")
+CAP_NAMES = ("none", "p99", "p90")
+
+
+def sweep(start: int, count: int, reps: int = 10, log=print) -> dict:
+    feats, times, slices, caps, tprs, nnz, n, names, idx = [], [], [], [], [], [], [], [], []
+    t0 = time.time()
+    for i in range(start, start + count):
+        A = gen.tuner_matrix(i)
+        table, best = tune_sweep(A, reps=reps)
+        feats.append(features(A))
+        times.append([e["ms"] if e["valid"] else np.inf for e in table])
+        slices.append([e["slice_rows"] for e in table])
+        caps.append([e["ell_width_cap"] for e in table])
+        tprs.append([e["ell_tpr"] for e in table])
+        nnz.append(A.nnz)
+        n.append(A.n)
+        names.append(A.name)
+        idx.append(i)
+        if (i - start) % 25 == 0:
+            log(f"[sweep] {i - start + 1}/{count} {A.name} n={A.n} nnz={A.nnz} best={best} "
+                f"{time.time() - t0:.0f}s")
+    return {"feats": np.array(feats, np.float32), "times": np.array(times), "slices": np.array(slices, np.int32),
+            "caps": np.array(caps, np.int32), "tprs": np.array(tprs, np.int32), "nnz": np.array(nnz, np.int64),
+            "n": np.array(n, np.int64), "names": np.array(names), "index": np.array(idx, np.int64)}
+
+
+def load(paths) -> dict:
+    parts = [dict(np.load(p, allow_pickle=False)) for p in paths]
+    return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+
+
+def targets(d: dict) -> np.ndarray:
+    """Per matrix: (log2 VecSize, cap index, log2 lanes, log ns per entry) of the fastest configuration."""
+    best = np.argmin(d["times"], axis=1)
+    rows = np.arange(len(best))
+    cap_idx = (best // 3) % 3
+    ns = d["times"][rows, best] * 1e6 / np.maximum(d["nnz"], 1)
+    return np.c_[np.log2(d["slices"][rows, best]), cap_idx, np.log2(d["tprs"][rows, best]), np.log(ns)].astype(
+        np.float32)
+
+
+def train(d: dict, epochs: int = 3000, lr: float = 3e-3, seed: int = 0, log=print) -> dict:
+    import torch
+
+    X = d["feats"].astype(np.float32)
+    T = targets(d)
+    fm, fs = X.mean(0), X.std(0)
+    fs = np.where(fs > 1e-6, fs, 1.0).astype(np.float32)
+    om, osd = T.mean(0), T.std(0)
+    osd = np.where(osd > 1e-6, osd, 1.0).astype(np.float32)
+    Xn = torch.from_numpy((X - fm) / fs).cuda()
+    Tn = torch.from_numpy((T - om) / osd).cuda()
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((64, 16), (64, 64), (4, 64)):   # He-uniform weights, zero biases
+        b = math.sqrt(6.0 / fan_in)
+        parts += [rng.uniform(-b, b, fan_out * fan_in), np.zeros(fan_out)]
+    net = Mlp(torch.from_numpy(np.concatenate(parts).astype(np.float32)))
+    hist = []
+    for ep in range(1, epochs + 1):
+        loss, _ = net.loss_grad(Xn, Tn)
+        net.adam(lr=lr)
+        if ep % 500 == 0 or ep == 1:
+            hist.append((ep, float(loss.item())))
+            log(f"[train] epoch {ep} loss {hist[-1][1]:.4f}")
+    return {"params": net.params.cpu().numpy(), "feat_mean": fm.astype(np.float32), "feat_std": fs,
+            "out_mean": om.astype(np.float32), "out_std": osd, "loss_history": np.array(hist, np.float64)}
+
+
+def save_model(m: dict, path: str = MODEL_PATH):
+    np.savez(path, **m)
+
+
+def load_model(path: str = MODEL_PATH) -> dict:
+    with np.load(path) as z:
+        return {k: z[k] for k in z.files}
+
+
+def install(path: str = MODEL_PATH):
+    """Load the saved model into the library (plans created with tuner=1 use it)."""
+    m = load_model(path)
+    tuner_set_model(m["params"], m["feat_mean"], m["feat_std"], m["out_mean"], m["out_std"])
+
+
+def evaluate(m: dict, d: dict, log=print) -> dict:
+    tuner_set_model(m["params"], m["feat_mean"], m["feat_std"], m["out_mean"], m["out_std"])
+    r_model, r_eq1, picks = [], [], []
+    for k, i in enumerate(d["index"]):
+        A = gen.tuner_matrix(int(i))
+        sr, cap, tpr, _ = tuner_predict(A)
+        cfg = list(zip(d["slices"][k], d["caps"][k], d["tprs"][k]))
+        g = cfg.index((sr, cap, tpr))
+        best = np.min(d["times"][k])
+        r_model.append(d["times"][k][g] / best)
+        r_eq1.append(d["times"][k][0] / best)     # grid entry 0: Eq. 1 VecSize, no cap, one lane per row
+        picks.append(g)
+    r_model, r_eq1 = np.array(r_model), np.array(r_eq1)
+
+    def summary(r):
+        return {"geomean": float(np.exp(np.mean(np.log(r)))), "p90": float(np.quantile(r, 0.9)),
+                "max": float(r.max()), "within_10pct": float(np.mean(r <= 1.10))}
+    out = {"matrices": int(len(r_model)), "learned": summary(r_model), "eq1_default": summary(r_eq1),
+           "gain_vs_eq1_geomean": float(np.exp(np.mean(np.log(r_eq1 / r_model))))}
+    log("[evaluate] " + json.dumps(out))
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    a = sub.add_parser("sweep")
+    a.add_argument("--start", type=int, required=True)
+    a.add_argument("--count", type=int, required=True)
+    a.add_argument("--reps", type=int, default=10)
+    a.add_argument("--out", required=True)
+    b = sub.add_parser("train")
+    b.add_argument("--data", nargs="+", required=True)
+    b.add_argument("--epochs", type=int, default=3000)
+    b.add_argument("--lr", type=float, default=3e-3)
+    b.add_argument("--out", default=MODEL_PATH)
+    c = sub.add_parser("evaluate")
+    c.add_argument("--model", default=MODEL_PATH)
+    c.add_argument("--data", nargs="+", required=True)
+    c.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    if args.cmd == "sweep":
+        np.savez(args.out, **sweep(args.start, args.count, args.reps))
+    elif args.cmd == "train":
+        m = train(load(args.data), epochs=args.epochs, lr=args.lr)
+        save_model(m, args.out)
+    else:
+        res = evaluate(load_model(args.model), load(args.data))
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(res, f)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
