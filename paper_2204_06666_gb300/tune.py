@@ -65,9 +65,17 @@ def load(paths) -> dict:
     return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
 
 
+def target_configs(d: dict, tie: float = 1.02) -> np.ndarray:
+    """Per matrix, the first grid configuration (grid order: VecSize, then cap, then lanes) whose time is within
+    `tie` of the fastest one: small matrices sit at a launch floor where many configurations tie, and the
+    first of them is the simplest."""
+    t = d["times"]
+    return np.argmax(t <= tie * t.min(axis=1, keepdims=True), axis=1)
+
+
 def targets(d: dict) -> np.ndarray:
-    """Per matrix: (log2 VecSize, cap index, log2 lanes, log ns per entry) of the fastest configuration."""
-    best = np.argmin(d["times"], axis=1)
+    """Per matrix: (log2 VecSize, cap index, log2 lanes, log ns per entry) of the target configuration."""
+    best = target_configs(d)
     rows = np.arange(len(best))
     cap_idx = (best // 3) % 3
     ns = d["times"][rows, best] * 1e6 / np.maximum(d["nnz"], 1)

@@ -131,3 +131,28 @@ def test_learned_choice_kept_and_fallback(eh):
         eh.tuner_set_model(None, None, None, None, None)
     R = eh.Plan(A, tuner=1)                          # no model loaded: the sweep decides
     assert R.info()["tuner_path"] == 2
+
+
+def test_trained_model_gains_over_eq1_default_on_heldout(eh):
+    # the committed network (trained on the GPU by the library's MLP kernels on sweeps of matrices
+    # 0..1999) against fresh sweeps of held-out matrices 5000..5011 (six FEM-like, six power-law)
+    from paper_2204_06666_gb300 import tune
+    tune.install()
+    try:
+        r_model, r_eq1 = [], []
+        for i in range(5000, 5012):
+            A = gen.tuner_matrix(i)
+            table, best = eh.tune_sweep(A, reps=10)
+            t = np.array([e["ms"] for e in table])
+            sr, cap, tpr, _ = eh.tuner_predict(A)
+            g = [(e["slice_rows"], e["ell_width_cap"], e["ell_tpr"]) for e in table].index((sr, cap, tpr))
+            r_model.append(t[g] / t.min())
+            r_eq1.append(t[0] / t.min())       # the method without the tuner: Eq. 1 VecSize, no cap, 1 lane
+        gm_model = float(np.exp(np.mean(np.log(r_model))))
+        gm_eq1 = float(np.exp(np.mean(np.log(r_eq1))))
+        assert gm_model <= 1.10, r_model        # within 10% of the best swept configuration
+        assert gm_eq1 / gm_model >= 1.3, (gm_eq1, gm_model)
+        P = eh.Plan(gen.tuner_matrix(5001), tuner=1)    # plan creation through the model
+        assert P.info()["tuner_path"] in (1, 3)
+    finally:
+        eh.tuner_set_model(None, None, None, None, None)
