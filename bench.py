@@ -140,6 +140,38 @@ def cpu_baseline(A, x, budget_s: float = 10.0):
             "sample": f"{rows} rows in blocks of {block} of the same matrix (plain C CSR, 1 thread, {dt:.1f} s)"}
 
 
+def kernel_source_sha() -> str:
+    """Hash of the sources that decide the fused kernel's memory traffic (kernel body, launch, layout)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu",
+                "paper_2204_06666_gb300/csrc/plan.cpp"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu capture, or None when the kernel's
+    sources changed since the capture (or no capture exists for this workload)."""
+    p = os.path.join(ROOT, "profiles", "ehyb_kernel_dram.json")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as f:
+        rec = json.load(f)
+    r = rec.get(workload)
+    if not r or r.get("source_sha") != kernel_source_sha():
+        return None, None
+    return float(r["dram_bytes_per_launch"]), r.get("note")
+
+
+def aggregate(local_ms: float, world: int, units_per_rank: float, reduce_max=None):
+    """Whole-job throughput: the max of the ranks' times, all ranks' units.  reduce_max(x) returns the max of
+    x over ranks (identity for one rank).  Returns (value in units/s, max ms)."""
+    ms_max = reduce_max(local_ms) if reduce_max else local_ms
+    return units_per_rank * world / (ms_max / 1e3), ms_max
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -235,12 +267,13 @@ def run_ehyb(args):
     kern_ms, kern_n = plan.profile_read()
     plan.profile_enable(False)
     clocks = clk.summary()
-    ms_max = ms
-    if pg:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+
+    def reduce_max(v):
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = flops_per_step * args.steps * world / (ms_max / 1e3) / 1e9
+        return float(t.item())
+    value, ms_max = aggregate(ms, world, flops_per_step * args.steps, reduce_max if pg else None)
+    value /= 1e9
     ms_per_step = ms_max / args.steps
 
     # ---- roofline of the fused kernel (its own per-launch event times from the timed region)
@@ -261,6 +294,11 @@ def run_ehyb(args):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": None, "peak_source": f"{peak_src} copy bandwidth",
                 "alu": {"achieved": fp64_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak}}
+    traffic, tnote = recorded_traffic(args.workload)
+    roof["traffic"] = traffic
+    if traffic is not None:
+        roof["traffic_over_algorithmic"] = traffic / bytes_alg
+        roof["traffic_source"] = tnote
     roof["kernel"] = "ehyb_kernel<double,double,scatter>"
     roof["kernel_ms"] = kern_s * 1e3
     roof["bytes_per_launch"] = bytes_alg

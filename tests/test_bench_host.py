@@ -1,0 +1,72 @@
+"""bench.py host logic without a GPU: the whole-job aggregation over ranks (gloo, world size 2), the
+traffic record's invalidation, and the reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+
+    def reduce_max(v):
+        t = torch.tensor([v], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    local_ms = [120.0, 150.0][rank]                     # the slower rank sets the time
+    value, ms_max = bench.aggregate(local_ms, world, 1e9, reduce_max)
+    out[rank] = (value, ms_max)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_max_over_ranks_gloo():
+    world = 2
+    out = mp.Manager().dict()
+    mp.spawn(_rank, args=(world, 29517, out), nprocs=world, join=True)
+    for r in range(world):
+        value, ms_max = out[r]
+        assert ms_max == 150.0
+        assert value == pytest.approx(2 * 1e9 / 0.150)   # all ranks' units over the slowest rank's time
+
+
+def test_aggregate_single_rank():
+    assert bench.aggregate(100.0, 1, 5e8) == (5e8 / 0.1, 100.0)
+
+
+def test_traffic_record_tied_to_kernel_sources(tmp_path, monkeypatch):
+    rec = {"hex_elast3d_70": {"source_sha": bench.kernel_source_sha(), "dram_bytes_per_launch": 9.0e8,
+                              "note": "x"}}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ehyb_kernel_dram.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the hash is computed over ROOT's sources: copy them so the record matches
+    for rel in ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu",
+                "paper_2204_06666_gb300/csrc/plan.cpp"):
+        dst = tmp_path / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    assert bench.recorded_traffic("hex_elast3d_70")[0] == 9.0e8
+    assert bench.recorded_traffic("fem2d_p1_200")[0] is None
+    (tmp_path / "paper_2204_06666_gb300/csrc/ehyb_core.cuh").write_text("// changed kernel")
+    assert bench.recorded_traffic("hex_elast3d_70")[0] is None     # kernel changed: no stale traffic
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "fem2d_p1_200", "--steps", "20", "--warmup", "3"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GFLOP/s" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
