@@ -368,6 +368,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     const size_t o_erv16 = A.add<uint16_t>(H.er_val_bf16.size());
     const size_t o_esp = A.add<int64_t>(H.er_slice_pos.size());
     const size_t o_esc = A.add<int32_t>(H.er_scol.size());
+    const size_t o_eso = A.add<int32_t>(H.er_scol_old.size());
     const size_t o_esv = A.add<double>(H.er_sval.size());
     const size_t o_esv32 = A.add<float>(H.er_sval_f32.size());
     const size_t o_esv16 = A.add<uint16_t>(H.er_sval_bf16.size());
@@ -388,7 +389,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     UP(o_n2o, H.new_to_old) UP(o_pp, H.part_ptr) UP(o_sp, H.slice_ptr) UP(o_pos, H.slice_pos) UP(o_ec, H.ell_col)
     UP(o_ev, H.ell_val) UP(o_ev32, H.ell_val_f32) UP(o_ev16, H.ell_val_bf16) UP(o_epp, H.er_part_ptr)
     UP(o_er, H.er_row) UP(o_erp, H.er_ptr) UP(o_erc, H.er_col) UP(o_erv, H.er_val) UP(o_erv32, H.er_val_f32)
-    UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_esc, H.er_scol) UP(o_esv, H.er_sval)
+    UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_esc, H.er_scol) UP(o_eso, H.er_scol_old) UP(o_esv, H.er_sval)
     UP(o_esv32, H.er_sval_f32) UP(o_esv16, H.er_sval_bf16)
 #undef UP
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_st, 0, 16, s);
@@ -416,6 +417,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     D.er_val_bf16 = (const uint16_t*)(base + o_erv16);
     D.er_slice_pos = (const int64_t*)(base + o_esp);
     D.er_scol = (const int32_t*)(base + o_esc);
+    D.er_scol_old = (const int32_t*)(base + o_eso);
     D.er_sval = (const double*)(base + o_esv);
     D.er_sval_f32 = (const float*)(base + o_esv32);
     D.er_sval_bf16 = (const uint16_t*)(base + o_esv16);
@@ -436,6 +438,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     std::vector<float>().swap(h.er_val_f32);
     std::vector<uint16_t>().swap(h.er_val_bf16);
     std::vector<int32_t>().swap(h.er_scol);
+    std::vector<int32_t>().swap(h.er_scol_old);
     std::vector<double>().swap(h.er_sval);
     std::vector<float>().swap(h.er_sval_f32);
     std::vector<uint16_t>().swap(h.er_sval_bf16);
@@ -512,8 +515,13 @@ ehyb_status_t ehyb_spmv(ehyb_plan_t p, const double* x, double* y, void* stream)
   if (p->dev.n == 0) return EHYB_OK;
   if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_permute_f64(p->dev, 1, x, p->xp, s));
   std::pair<cudaEvent_t, cudaEvent_t>* slot;
+  if (p->dev.er_layout == 0) {  // one launch: the permutation of x is fused into the kernel's loads
+    if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
+    CK(launch_ehyb_f64(p->dev, x, y, 2, s));
+    return record_end(slot, s);
+  }
+  CK(launch_permute_f64(p->dev, 1, x, p->xp, s));
   if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
   CK(launch_ehyb_f64(p->dev, p->xp, y, 1, s));
   return record_end(slot, s);
@@ -553,8 +561,13 @@ ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t p, const float* x, float* y, void* stre
   if (p->dev.n == 0) return EHYB_OK;
   if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_permute_f32(p->dev, 1, x, p->xp32, s));
   std::pair<cudaEvent_t, cudaEvent_t>* slot;
+  if (p->dev.er_layout == 0) {
+    if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
+    CK(launch_ehyb_lowp(p->dev, p->lowp, x, y, 2, s));
+    return record_end(slot, s);
+  }
+  CK(launch_permute_f32(p->dev, 1, x, p->xp32, s));
   if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
   CK(launch_ehyb_lowp(p->dev, p->lowp, p->xp32, y, 1, s));
   return record_end(slot, s);

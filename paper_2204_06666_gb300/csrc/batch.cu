@@ -4,11 +4,11 @@
 // processing-time order).  A grid of (SMs x resident blocks) blocks pulls tiles from one atomic
 // counter and runs each with the same per-partition code as the single-plan kernel
 // (core::partition_spmv), so every row is summed in exactly the same order as by ehyb_spmv: the
-// batch result equals the per-plan results bit for bit.  The block's mbarrier is re-armed for every
-// tile (phase tracked in shared memory, async-proxy fence before the buffer is reused).  The last
-// block to leave resets the counter, so the launch sequence -- one gather kernel over all plans
-// (x_p = x[new_to_old], plan index in blockIdx.y) and the persistent kernel -- is captured once into a
-// CUDA graph and replayed; a call only rewrites the table of x / y pointers when they change.
+// batch result equals the per-plan results bit for bit.  Each tile stages its slice of x straight from
+// the caller's x through the plan's new_to_old (the permutation is fused into the loads, as in
+// ehyb_spmv), so the batch is ONE launch.  The last block to leave resets the counter, so the launch is
+// captured once into a CUDA graph and replayed; a call only rewrites the table of x / y pointers when
+// they change.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,19 +29,11 @@ struct BatchPlan {
   const double* ell_val;
   const double* er_val;
   const double* x;  // caller's x (original numbering)
-  double* xp;       // the plan's workspace (plan numbering)
   double* y;        // caller's y (original numbering)
   int64_t n;
 };
 
 constexpr int kBatchThreads = 512;
-
-__global__ void batch_permute_kernel(const BatchPlan* __restrict__ plans) {
-  const BatchPlan& bp = plans[blockIdx.y];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < bp.n; i += stride)
-    bp.xp[i] = __ldg(bp.x + bp.a.new_to_old[i]);
-}
 
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchPlan* __restrict__ plans,
                                                               const int2* __restrict__ tiles, int ntiles,
@@ -61,8 +53,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchPlan* _
     if (t >= ntiles) break;
     const int2 tl = tiles[t];
     const BatchPlan& bp = plans[tl.x];
-    if (!partition_spmv<double, double, true, true>(bp.a, bp.ell_val, bp.er_val, bp.xp, bp.y, tl.y,
-                                                    reinterpret_cast<double*>(smem_raw), bs))
+    if (!partition_spmv<double, double, true, true, false, true>(bp.a, bp.ell_val, bp.er_val, bp.x, bp.y, tl.y,
+                                                                 reinterpret_cast<double*>(smem_raw), bs))
       break;
   }
   __syncthreads();
@@ -92,7 +84,7 @@ struct ehyb_batch_s {
   BatchPlan* d_table = nullptr;
   int2* d_tiles = nullptr;
   int* d_counters = nullptr;
-  int ntiles = 0, grid = 0, perm_blocks = 1;
+  int ntiles = 0, grid = 0;
   size_t smem = 0;
   int64_t max_n = 0;
   cudaStream_t cap = nullptr;
@@ -134,7 +126,6 @@ extern "C" ehyb_status_t ehyb_batch_create(int32_t count, const ehyb_plan_t* pla
     bp.a = make_kargs(P->dev);
     bp.ell_val = P->dev.ell_val;
     bp.er_val = P->dev.er_sval;
-    bp.xp = P->xp;
     bp.n = P->dev.n;
     b->table.push_back(bp);
     b->max_n = std::max(b->max_n, P->dev.n);
@@ -167,7 +158,6 @@ extern "C" ehyb_status_t ehyb_batch_create(int32_t count, const ehyb_plan_t* pla
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b->smem);
   if (e != cudaSuccess) { batch_free(b); return cuda_error_status(e, "batch launch setup"); }
   b->grid = sms * std::max(per_sm, 1);
-  b->perm_blocks = (int)std::min<int64_t>(64, std::max<int64_t>(1, (b->max_n + 255) / 256));
 
   const size_t t_bytes = ((size_t)count * sizeof(BatchPlan) + 255) & ~(size_t)255;
   const size_t l_bytes = ((size_t)std::max(b->ntiles, 1) * sizeof(int2) + 255) & ~(size_t)255;
@@ -207,7 +197,6 @@ extern "C" ehyb_status_t ehyb_batch_spmv(ehyb_batch_t b, const double* const* xs
   if (!b->graph) {
     cudaGraph_t g;
     CKB(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    batch_permute_kernel<<<dim3((unsigned)b->perm_blocks, (unsigned)b->count), 256, 0, b->cap>>>(b->d_table);
     batch_kernel<<<b->grid, kBatchThreads, b->smem, b->cap>>>(b->d_table, b->d_tiles, b->ntiles, b->d_counters);
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);

@@ -29,6 +29,7 @@ struct DevPlan {
   int32_t er_layout = 0;  // 0: sliced with the slab slices; 1: CSR lines
   const int64_t* er_slice_pos = nullptr;
   const int32_t* er_scol = nullptr;
+  const int32_t* er_scol_old = nullptr;  // er_scol in the caller's numbering (x read in place)
   const double* er_sval = nullptr;
   const float* er_sval_f32 = nullptr;
   const uint16_t* er_sval_bf16 = nullptr;
@@ -44,8 +45,9 @@ size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes);
 cudaError_t launch_permute_f64(const DevPlan& P, int to_new, const double* in, double* out, cudaStream_t s);
 cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, float* out, cudaStream_t s);
 
-// Fused slab + ER kernel.  xp is in the plan numbering; y is written at new_to_old[r] when
-// scatter != 0, else at r.
+// Fused slab + ER kernel.  scatter 0: x and y in the plan numbering; 1: x in the plan numbering, y
+// written at new_to_old[r]; 2 (sliced ER layout only, else as 1): x and y both in the caller's numbering,
+// x read through new_to_old while it is staged.
 // Fused dot product sum_r y_r * xp_r in FP64 (sliced ER layout only): one partial per partition in
 // part[nparts]; the last block reduces them in a fixed order into *result and resets *arrive (zero).
 struct DotOut {

@@ -158,6 +158,7 @@ struct KArgs {
   int32_t tpr_log2, er_tpr_log2;
   const int64_t* er_slice_pos;
   const int32_t* er_scol;
+  const int32_t* er_scol_old;
   const int32_t* new_to_old;
   const int32_t* part_ptr;
   const int32_t* slice_ptr;
@@ -211,8 +212,13 @@ struct BlockState {
 };
 
 // One partition p of a plan: stage its slice of x_p, run its slab (and ER) slices, write y.
-// Returns false (uniformly across the block) when the staging wait ran out of time.
-template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false>
+// GATHER: x is given in the caller's numbering and the permutation into the plan numbering is fused
+// into the staging (xs[r - pb] = x[new_to_old[r]], plain loads) and into the ER gathers (columns in the
+// caller's numbering), so no permuted copy of x is written or read; otherwise x is x_p and the slice is
+// staged by one bulk asynchronous copy.
+// Returns false (uniformly across the block) when the staging wait ran
+// out of time.
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false, bool GATHER = false>
 __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
                                                const V* __restrict__ er_val, const X* __restrict__ xp,
                                                X* __restrict__ y, const int p, X* xs, BlockState& bs) {
@@ -230,7 +236,8 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
   const int a0 = pb & ~(EPV - 1);  // 16-byte aligned start
   const int a1 = pe & ~(EPV - 1);  // bulk part ends at the last aligned boundary <= pe
   const bool aligned_src = ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
-  const uint32_t bulk_bytes = (aligned_src && a1 > a0) ? (uint32_t)(a1 - a0) * (uint32_t)sizeof(X) : 0u;
+  const uint32_t bulk_bytes =
+      (!GATHER && aligned_src && a1 > a0) ? (uint32_t)(a1 - a0) * (uint32_t)sizeof(X) : 0u;
   if (tid == 0) {
     bs.slice_counter = s0 + nwarps;
     if (bulk_bytes) {
@@ -244,8 +251,22 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       if (!a.inject) bulk_g2s(xs, xp + a0, bulk_bytes, &bs.bar);
     }
   }
-  // plain loads: everything when the source is unaligned, else the ragged tail [a1, pe)
-  {
+  if (GATHER) {
+    // xs[r - a0] = x[new_to_old[r]]: kBatch indices, then kBatch values in flight per thread
+    const int bd = blockDim.x;
+    for (int i0 = pb + tid; i0 < pe; i0 += kBatch * bd) {
+      int c[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) c[u] = (i0 + u * bd < pe) ? __ldg(a.new_to_old + i0 + u * bd) : -1;
+      X v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) v[u] = c[u] >= 0 ? __ldg(xp + c[u]) : X(0);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (i0 + u * bd < pe) xs[i0 + u * bd - a0] = v[u];
+    }
+  } else {
+    // plain loads: everything when the source is unaligned, else the ragged tail [a1, pe)
     const int lo = bulk_bytes ? (a1 > pb ? a1 : pb) : pb;
     for (int i = lo + tid; i < pe; i += blockDim.x) xs[i - a0] = xp[i];
   }
@@ -309,7 +330,7 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       }
     }
     X acc = slab_dot<V, X>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
-    if (ER_SLICED) acc = er_dot<V, X>(er_val + epos + lane, a.er_scol + epos + lane, we, xp, acc);
+    if (ER_SLICED) acc = er_dot<V, X>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc);
     for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
     if (sub == 0 && row < pe) {
@@ -396,6 +417,7 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.er_tpr_log2 = ilog2(P.er_tpr);
   a.er_slice_pos = P.er_slice_pos;
   a.er_scol = P.er_scol;
+  a.er_scol_old = P.er_scol_old;
   a.new_to_old = P.new_to_old;
   a.part_ptr = P.part_ptr;
   a.slice_ptr = P.slice_ptr;

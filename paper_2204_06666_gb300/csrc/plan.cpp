@@ -335,12 +335,16 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   P.er_col.assign((size_t)er_nnz, 0);
   P.er_val.assign((size_t)er_nnz, 0.0);
   P.er_scol.assign((size_t)er_stored, 0);
+  P.er_scol_old.assign((size_t)er_stored, 0);
   P.er_sval.assign((size_t)er_stored, 0.0);
   // padding slots of the sliced ER part point at the first row of their partition (value 0)
   for (int32_t p = 0; p < nparts && P.er_layout == 0; ++p)
     for (int64_t k = P.er_slice_pos[(size_t)P.slice_ptr[(size_t)p]];
          k < P.er_slice_pos[(size_t)P.slice_ptr[(size_t)p + 1]]; ++k)
+    {
       P.er_scol[(size_t)k] = P.part_ptr[(size_t)p];
+      P.er_scol_old[(size_t)k] = P.new_to_old[(size_t)P.part_ptr[(size_t)p]];
+    }
   P.row_ell_count.resize((size_t)n);
   P.ell_nnz = 0;
   std::vector<int32_t> part_of_new((size_t)nparts > 0 ? (size_t)n : 0);
@@ -367,6 +371,7 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
       } else if (P.er_layout == 0) {
         const int64_t pos = ebase + 32 * (je / tpr) + lane0 + (int32_t)(je % tpr);
         P.er_scol[(size_t)pos] = P.old_to_new[(size_t)c];
+        P.er_scol_old[(size_t)pos] = c;
         P.er_sval[(size_t)pos] = val[k];
         ++je;
       } else {

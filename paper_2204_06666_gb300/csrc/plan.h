@@ -38,6 +38,7 @@ struct HostPlan {
   int32_t er_layout = 0;
   std::vector<int64_t> er_slice_pos;
   std::vector<int32_t> er_scol;
+  std::vector<int32_t> er_scol_old;  // the same columns in the caller's (original) numbering
   std::vector<double> er_sval;
   std::vector<float> er_sval_f32;
   std::vector<uint16_t> er_sval_bf16;

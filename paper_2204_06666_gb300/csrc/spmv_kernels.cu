@@ -11,7 +11,7 @@ namespace {
 
 using namespace core;
 
-template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT>
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false>
 __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
                                                     const V* __restrict__ er_val, const X* __restrict__ xp,
                                                     X* __restrict__ y) {
@@ -22,8 +22,8 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     bs.bar_ready = 0;
     bs.phase = 0;
   }
-  partition_spmv<V, X, SCATTER, ER_SLICED, DOT>(a, ell_val, er_val, xp, y, blockIdx.x,
-                                                reinterpret_cast<X*>(smem_raw), bs);
+  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER>(a, ell_val, er_val, xp, y, blockIdx.x,
+                                                        reinterpret_cast<X*>(smem_raw), bs);
 }
 
 template <typename X>
@@ -74,6 +74,7 @@ static cudaError_t set_smem(int bytes) {
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, false, false>, attr, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true>, attr, bytes))) return e;
   return cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true>, attr, bytes);
 }
 
@@ -110,6 +111,8 @@ static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const 
   const V* erv = sl ? erv_sl : erv_csr;
   if (dot) {  // the fused dot product exists for the sliced layout in the plan numbering (solver use)
     ehyb_kernel<V, X, false, true, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+  } else if (scatter == 2 && sl) {  // x in the caller's numbering, permutation fused into the loads
+    ehyb_kernel<V, X, true, true, false, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
   } else if (scatter) {
     if (sl) ehyb_kernel<V, X, true, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
     else ehyb_kernel<V, X, true, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);

@@ -122,6 +122,28 @@ def test_permuted_entry_and_permute(eh):
     assert np.array_equal(yp2.cpu().numpy(), yp.cpu().numpy())
 
 
+@pytest.mark.parametrize("opt", [dict(), dict(ell_tpr=4, slice_rows=300), dict(er_layout=1)])
+def test_fused_permutation_matches_permute_then_plan_numbering(eh, opt):
+    # ehyb_spmv reads x through new_to_old while staging (sliced ER) and must give the bits of the
+    # explicit route permute -> plan-numbering SpMV -> permute back, also for an x that is not 16-byte aligned
+    A = gen.tet_lap3d(N=18, dirichlet=False)
+    x = gen.uniform(A.n, 77)
+    P, y = _run(eh, A, x, **opt)
+    xd = torch.from_numpy(x).cuda()
+    xp, yp, back = torch.empty_like(xd), torch.empty_like(xd), torch.empty_like(xd)
+    P.permute(True, xd, xp)
+    P.spmv_permuted(xp, yp)
+    P.permute(False, yp, back)
+    big = torch.zeros(A.n + 1, dtype=torch.float64, device="cuda")
+    big[1:] = xd
+    y2 = torch.empty_like(xd)
+    P.spmv(big[1:], y2)
+    torch.cuda.synchronize()
+    assert np.array_equal(back.cpu().numpy(), y)
+    assert np.array_equal(y2.cpu().numpy(), y)
+    _check_fp(A, x, y)
+
+
 def test_host_entry_matches_device_entry(eh):
     A = gen.fem2d_p1(N=80)
     x = gen.uniform(A.n, 9)
@@ -206,11 +228,14 @@ def test_edge_cases(eh):
 def test_staging_wait_timeout_is_reported_and_context_survives(eh):
     A = gen.fem2d_p1(N=30)
     x = gen.uniform(A.n, 1)
-    # the wait is given a copy that is never issued: it must run out after 2 ms and report
+    # the wait is given a copy that is never issued: it must run out after 2 ms and report (the bulk
+    # staging copy is the one of the plan-numbering entry; ehyb_spmv gathers x with plain loads)
     P = eh.Plan(A, slice_rows=100, inject_wait_fault=1, wait_timeout_ns=2_000_000)
     xd = torch.from_numpy(x).cuda()
+    xp = torch.empty_like(xd)
+    P.permute(True, xd, xp)
     yd = torch.zeros_like(xd)
-    P.spmv(xd, yd)
+    P.spmv_permuted(xp, yd)
     assert P.check() == eh.EHYB_ERR_TIMEOUT
     assert P.check() == 0   # reading clears the word
     # the context is intact: a normal plan still computes correctly
