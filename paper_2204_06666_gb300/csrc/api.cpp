@@ -367,6 +367,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     const size_t o_erv32 = A.add<float>(H.er_val_f32.size());
     const size_t o_erv16 = A.add<uint16_t>(H.er_val_bf16.size());
     const size_t o_esp = A.add<int64_t>(H.er_slice_pos.size());
+    const size_t o_so = A.add<int32_t>(H.slice_order.size());
     const size_t o_esc = A.add<int32_t>(H.er_scol.size());
     const size_t o_eso = A.add<int32_t>(H.er_scol_old.size());
     const size_t o_esv = A.add<double>(H.er_sval.size());
@@ -389,7 +390,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     UP(o_n2o, H.new_to_old) UP(o_pp, H.part_ptr) UP(o_sp, H.slice_ptr) UP(o_pos, H.slice_pos) UP(o_ec, H.ell_col)
     UP(o_ev, H.ell_val) UP(o_ev32, H.ell_val_f32) UP(o_ev16, H.ell_val_bf16) UP(o_epp, H.er_part_ptr)
     UP(o_er, H.er_row) UP(o_erp, H.er_ptr) UP(o_erc, H.er_col) UP(o_erv, H.er_val) UP(o_erv32, H.er_val_f32)
-    UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_esc, H.er_scol) UP(o_eso, H.er_scol_old) UP(o_esv, H.er_sval)
+    UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_so, H.slice_order) UP(o_esc, H.er_scol) UP(o_eso, H.er_scol_old) UP(o_esv, H.er_sval)
     UP(o_esv32, H.er_sval_f32) UP(o_esv16, H.er_sval_bf16)
 #undef UP
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_st, 0, 16, s);
@@ -416,6 +417,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     D.er_val_f32 = (const float*)(base + o_erv32);
     D.er_val_bf16 = (const uint16_t*)(base + o_erv16);
     D.er_slice_pos = (const int64_t*)(base + o_esp);
+    D.slice_order = (const int32_t*)(base + o_so);
     D.er_scol = (const int32_t*)(base + o_esc);
     D.er_scol_old = (const int32_t*)(base + o_eso);
     D.er_sval = (const double*)(base + o_esv);

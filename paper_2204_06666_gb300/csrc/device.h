@@ -15,6 +15,7 @@ struct DevPlan {
   const int32_t* part_ptr = nullptr;
   const int32_t* slice_ptr = nullptr;
   const int64_t* slice_pos = nullptr;
+  const int32_t* slice_order = nullptr;  // per partition, slices in processing order (longest first)
   const uint16_t* ell_col = nullptr;
   const double* ell_val = nullptr;
   const float* ell_val_f32 = nullptr;

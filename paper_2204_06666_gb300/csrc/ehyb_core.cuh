@@ -105,7 +105,8 @@ __device__ __forceinline__ float load_val<uint16_t, float>(const uint16_t* p) {
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
-constexpr int kBatch = 8;  // slots whose loads are issued before their FMAs
+constexpr int kBatch = 8;   // slots whose loads are issued before their FMAs
+constexpr int kStage = 16;  // elements of x per thread in flight while a slice of x is gathered
 
 // acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory.  Loads are issued
 // kBatch at a time ahead of their FMAs; the FMAs run in slot order.  (A predicated last batch measured
@@ -163,6 +164,7 @@ struct KArgs {
   const int32_t* part_ptr;
   const int32_t* slice_ptr;
   const int64_t* slice_pos;
+  const int32_t* slice_order;
   const uint16_t* ell_col;
   const int32_t* er_part_ptr;
   const int32_t* er_row;
@@ -252,17 +254,18 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     }
   }
   if (GATHER) {
-    // xs[r - a0] = x[new_to_old[r]]: kBatch indices, then kBatch values in flight per thread
+    // xs[r - a0] = x[new_to_old[r]]: kStage indices, then kStage values in flight per thread (one round
+    // covers a partition of kStage * blockDim rows)
     const int bd = blockDim.x;
-    for (int i0 = pb + tid; i0 < pe; i0 += kBatch * bd) {
-      int c[kBatch];
+    for (int i0 = pb + tid; i0 < pe; i0 += kStage * bd) {
+      int c[kStage];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) c[u] = (i0 + u * bd < pe) ? __ldg(a.new_to_old + i0 + u * bd) : -1;
-      X v[kBatch];
+      for (int u = 0; u < kStage; ++u) c[u] = (i0 + u * bd < pe) ? __ldg(a.new_to_old + i0 + u * bd) : -1;
+      X v[kStage];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) v[u] = c[u] >= 0 ? __ldg(xp + c[u]) : X(0);
+      for (int u = 0; u < kStage; ++u) v[u] = c[u] >= 0 ? __ldg(xp + c[u]) : X(0);
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u)
+      for (int u = 0; u < kStage; ++u)
         if (i0 + u * bd < pe) xs[i0 + u * bd - a0] = v[u];
     }
   } else {
@@ -298,10 +301,11 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
   // (static round-robin when the fused dot product is requested, so its order is fixed)
   constexpr bool dot = DOT;  // a.dot_part is set
   double dacc = 0.0;
-  int s = s0 + warp;
+  int i = s0 + warp;  // position in the partition's processing order
+  int s = i < s1 ? a.slice_order[i] : s1;
   int64_t pos = 0, epos = 0;
   int w = 0, we = 0;
-  if (s < s1) {
+  if (i < s1) {
     pos = a.slice_pos[s];
     w = (int)((a.slice_pos[s + 1] - pos) >> 5);
     if (ER_SLICED) {
@@ -309,19 +313,20 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       we = (int)((a.er_slice_pos[s + 1] - epos) >> 5);
     }
   }
-  while (s < s1) {
+  while (i < s1) {
     // reserve the next slice and start its metadata loads before working on this one
-    int nxt;
+    int inxt;
     if (dot) {
-      nxt = s + nwarps;
+      inxt = i + nwarps;
     } else {
       int t = 0;
       if (lane == 0) t = atomicAdd(&bs.slice_counter, 1);
-      nxt = __shfl_sync(FULL, t, 0);
+      inxt = __shfl_sync(FULL, t, 0);
     }
+    const int nxt = inxt < s1 ? a.slice_order[inxt] : s1;
     int64_t npos = 0, nepos = 0;
     int nw = 0, nwe = 0;
-    if (nxt < s1) {
+    if (inxt < s1) {
       npos = a.slice_pos[nxt];
       nw = (int)((a.slice_pos[nxt + 1] - npos) >> 5);
       if (ER_SLICED) {
@@ -338,6 +343,7 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       else y[row] = acc;
       if (dot) dacc = fma((double)acc, (double)xsl[row - pb], dacc);
     }
+    i = inxt;
     s = nxt;
     pos = npos;
     w = nw;
@@ -422,6 +428,7 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.part_ptr = P.part_ptr;
   a.slice_ptr = P.slice_ptr;
   a.slice_pos = P.slice_pos;
+  a.slice_order = P.slice_order;
   a.ell_col = P.ell_col;
   a.er_part_ptr = P.er_part_ptr;
   a.er_row = P.er_row;

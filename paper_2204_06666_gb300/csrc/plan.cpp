@@ -307,6 +307,20 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   }
   const int64_t er_stored = P.er_slice_pos[(size_t)P.nslices];
 
+  // processing order of the slices inside each partition: longest estimated work first (an ER slot
+  // gathers x from global memory and is counted twice)
+  P.slice_order.resize((size_t)P.nslices);
+  for (int32_t p = 0; p < nparts; ++p) {
+    const int32_t s0 = P.slice_ptr[(size_t)p], s1 = P.slice_ptr[(size_t)p + 1];
+    auto work = [&](int32_t s) {
+      return (P.slice_pos[(size_t)s + 1] - P.slice_pos[(size_t)s]) +
+             2 * (P.er_slice_pos[(size_t)s + 1] - P.er_slice_pos[(size_t)s]);
+    };
+    for (int32_t s = s0; s < s1; ++s) P.slice_order[(size_t)s] = s;
+    std::stable_sort(P.slice_order.begin() + s0, P.slice_order.begin() + s1,
+                     [&](int32_t u, int32_t v) { return work(u) > work(v); });
+  }
+
   // er_layout 1: ER lines (rows with extra entries), per partition, sorted by ER count descending
   P.er_part_ptr.assign((size_t)nparts + 1, 0);
   P.er_row.clear();

@@ -22,6 +22,10 @@ struct HostPlan {
   std::vector<int32_t> new_to_old, old_to_new;
   std::vector<int32_t> part_ptr, slice_ptr;
   std::vector<int64_t> slice_pos;
+  // processing order: per partition, its slice ids by decreasing estimated work (slab width + 2 x sliced
+  // ER width, ties by id), so the warps of a block take the long slices first and the block's tail
+  // consists of short ones
+  std::vector<int32_t> slice_order;
   std::vector<uint16_t> ell_col;
   std::vector<double> ell_val;
   std::vector<float> ell_val_f32;
