@@ -17,6 +17,13 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
                                                     X* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ BlockState bs;
+  // Launched with programmatic stream serialization: the next kernel in the stream may be scheduled at
+  // once, so its blocks become resident as this grid's blocks leave and its launch latency overlaps
+  // this grid's tail.  Nothing is read or written before pdl_wait(), which returns when the previous
+  // kernel in the stream has completed and its writes are visible.  (An L2 bulk prefetch of each
+  // warp's first slice before the wait measured slower on the hex workload and is not done.)
+  pdl_launch_dependents();
+  pdl_wait();
   if (a.skip && *a.skip) return;
   if (threadIdx.x == 0) {
     bs.bar_ready = 0;
@@ -97,6 +104,23 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
   return cudaGetLastError();
 }
 
+// every fused-kernel launch carries the programmatic-stream-serialization attribute (see ehyb_kernel)
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false>
+static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArgs& a, const V* ev, const V* erv,
+                       const X* xp, X* y) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)P.nparts);
+  cfg.blockDim = dim3((unsigned)P.threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
+}
+
 template <typename V, typename X>
 static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const V* erv_sl, const X* xp, X* y,
                          int scatter, size_t smem, cudaStream_t s, const DotOut* dot, const int32_t* skip) {
@@ -110,15 +134,15 @@ static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const 
   const bool sl = P.er_layout == 0;
   const V* erv = sl ? erv_sl : erv_csr;
   if (dot) {  // the fused dot product exists for the sliced layout in the plan numbering (solver use)
-    ehyb_kernel<V, X, false, true, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    launch_pdl<V, X, false, true, true>(P, smem, s, a, ev, erv, xp, y);
   } else if (scatter == 2 && sl) {  // x in the caller's numbering, permutation fused into the loads
-    ehyb_kernel<V, X, true, true, false, true><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    launch_pdl<V, X, true, true, false, true>(P, smem, s, a, ev, erv, xp, y);
   } else if (scatter) {
-    if (sl) ehyb_kernel<V, X, true, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
-    else ehyb_kernel<V, X, true, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    if (sl) launch_pdl<V, X, true, true, false>(P, smem, s, a, ev, erv, xp, y);
+    else launch_pdl<V, X, true, false, false>(P, smem, s, a, ev, erv, xp, y);
   } else {
-    if (sl) ehyb_kernel<V, X, false, true, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
-    else ehyb_kernel<V, X, false, false, false><<<P.nparts, P.threads, smem, s>>>(a, ev, erv, xp, y);
+    if (sl) launch_pdl<V, X, false, true, false>(P, smem, s, a, ev, erv, xp, y);
+    else launch_pdl<V, X, false, false, false>(P, smem, s, a, ev, erv, xp, y);
   }
 }
 

@@ -144,6 +144,32 @@ def test_fused_permutation_matches_permute_then_plan_numbering(eh, opt):
     _check_fp(A, x, y)
 
 
+def test_back_to_back_launches_respect_the_stream_order(eh):
+    # consecutive launches may be scheduled early (programmatic dependent launch): a chain in which each
+    # SpMV reads the previous one's output, with no host synchronisation, must still see finished inputs
+    A = gen.hex_elast3d(N=14)
+    x = gen.uniform(A.n, 3)
+    P = eh.Plan(A)
+    v = [torch.from_numpy(x).cuda()] + [torch.empty(A.n, dtype=torch.float64, device="cuda") for _ in range(6)]
+    for k in range(6):
+        P.spmv(v[k], v[k + 1])
+    xp = [torch.empty_like(v[0]) for _ in range(4)]
+    P.permute(True, v[6], xp[0])
+    for k in range(3):
+        P.spmv_permuted(xp[k], xp[k + 1])
+    back = torch.empty_like(v[0])
+    P.permute(False, xp[3], back)
+    torch.cuda.synchronize()
+    ref = x.copy()
+    for k in range(6):
+        ref = oracle.spmv(A, ref)
+        got = v[k + 1].cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), k
+    for k in range(3):
+        ref = oracle.spmv(A, ref)
+    assert np.linalg.norm(back.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_host_entry_matches_device_entry(eh):
     A = gen.fem2d_p1(N=80)
     x = gen.uniform(A.n, 9)
