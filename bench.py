@@ -472,7 +472,7 @@ def run_batch(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     mats = gen.fem_batch(count=args.batch_count, seed=31)
-    plans = [eh.Plan(A, part_nnz=args.part_nnz) for A in mats]
+    plans = [eh.Plan(A, part_nnz=args.part_nnz, smem_budget=args.batch_smem) for A in mats]
     xs = [torch.from_numpy(gen.uniform(A.n, 32 + i)).cuda() for i, A in enumerate(mats)]
     ys = [torch.empty_like(x) for x in xs]
     B = eh.Batch(plans)
@@ -494,7 +494,8 @@ def run_batch(args):
             "config": {"workload": f"fem_batch_{args.batch_count}", "matrices": len(mats),
                        "rows": sum(A.n for A in mats), "nnz": nnz, "n_min": min(A.n for A in mats),
                        "n_max": max(A.n for A in mats), "kinds": sorted(set(A.name.split("_N")[0] for A in mats)),
-                       "tiles": B.info()["tiles"], "grid": B.info()["grid"], "part_nnz": args.part_nnz},
+                       "tiles": B.info()["tiles"], "grid": B.info()["grid"], "threads": B.info()["threads"],
+                       "part_nnz": args.part_nnz, "smem_budget": args.batch_smem},
             "batch": {"ms": t_batch, "gflops": 2 * nnz / t_batch / 1e6, "effective_gbs": byts / t_batch / 1e6},
             "one_by_one": {"ms": t_seq, "gflops": 2 * nnz / t_seq / 1e6, "effective_gbs": byts / t_seq / 1e6,
                            "launches": len(mats)},
@@ -563,7 +564,9 @@ def main():
     ap.add_argument("--solver", action="store_true", help="time CG / refined CG instead of the SpMV")
     ap.add_argument("--batch", action="store_true", help="time the batched launch over generated FEM matrices")
     ap.add_argument("--batch-count", type=int, default=64)
-    ap.add_argument("--part-nnz", type=int, default=160000, help="entries per partition of batched plans")
+    ap.add_argument("--part-nnz", type=int, default=640000, help="entries per partition of batched plans")
+    ap.add_argument("--batch-smem", type=int, default=50000,
+                    help="shared-memory budget per block of batched plans in bytes (caps partition rows; 0 = device max)")
     ap.add_argument("--spmm", action="store_true", help="time SpMM with --spmm-k right-hand sides")
     ap.add_argument("--spmm-k", type=int, nargs="+", default=[8, 32])
     ap.add_argument("--solver-reps", type=int, default=3)

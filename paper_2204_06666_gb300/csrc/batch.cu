@@ -33,9 +33,9 @@ struct BatchPlan {
   int64_t n;
 };
 
-constexpr int kBatchThreads = 512;
+constexpr int kMaxThreads = 1024;  // block size: 512 when two or more blocks fit an SM, else 1024
 
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchPlan* __restrict__ plans,
+__global__ void __launch_bounds__(kMaxThreads, 1) batch_kernel(const BatchPlan* __restrict__ plans,
                                                               const int2* __restrict__ tiles, int ntiles,
                                                               int* counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -84,7 +84,7 @@ struct ehyb_batch_s {
   BatchPlan* d_table = nullptr;
   int2* d_tiles = nullptr;
   int* d_counters = nullptr;
-  int ntiles = 0, grid = 0;
+  int ntiles = 0, grid = 0, threads = 512;
   size_t smem = 0;
   int64_t max_n = 0;
   cudaStream_t cap = nullptr;
@@ -155,7 +155,13 @@ extern "C" ehyb_status_t ehyb_batch_create(int32_t count, const ehyb_plan_t* pla
   int sms = 0, per_sm = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b->smem);
+  // 512 threads while two blocks fit an SM (one block's staging overlaps the other's slices), otherwise
+  // one block of 1024 threads per SM (32 warps keep enough loads in flight)
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, 512, b->smem);
+  if (e == cudaSuccess && per_sm < 2) {
+    b->threads = kMaxThreads;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kMaxThreads, b->smem);
+  }
   if (e != cudaSuccess) { batch_free(b); return cuda_error_status(e, "batch launch setup"); }
   b->grid = sms * std::max(per_sm, 1);
 
@@ -197,7 +203,7 @@ extern "C" ehyb_status_t ehyb_batch_spmv(ehyb_batch_t b, const double* const* xs
   if (!b->graph) {
     cudaGraph_t g;
     CKB(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    batch_kernel<<<b->grid, kBatchThreads, b->smem, b->cap>>>(b->d_table, b->d_tiles, b->ntiles, b->d_counters);
+    batch_kernel<<<b->grid, b->threads, b->smem, b->cap>>>(b->d_table, b->d_tiles, b->ntiles, b->d_counters);
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     CKB(e1);
@@ -214,7 +220,7 @@ extern "C" ehyb_status_t ehyb_batch_info(ehyb_batch_t b, int32_t* ntiles, int32_
   if (!b) return EHYB_ERR_INVALID_ARG;
   if (ntiles) *ntiles = b->ntiles;
   if (grid) *grid = b->grid;
-  if (threads) *threads = kBatchThreads;
+  if (threads) *threads = b->threads;
   return EHYB_OK;
 }
 
