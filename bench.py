@@ -346,6 +346,28 @@ def run_ehyb(args):
             base.close()
         csr["ehyb_speedup_vs_best_csr"] = min(c["ms"] for c in csr.values() if isinstance(c, dict)) / ms_per_step
 
+    # ---- plan file: save once, load (no partitioning / encoding), same bits
+    plan_io = None
+    if args.plan_io:
+        import tempfile as _tf
+        d = _tf.mkdtemp()
+        path = os.path.join(d, "plan.ehyb")
+        t0 = time.perf_counter()
+        plan.save(path)
+        save_ms = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        loaded = eh.Plan.load(path)
+        load_ms = (time.perf_counter() - t0) * 1e3
+        y2 = torch.empty_like(yd)
+        loaded.spmv(xd, y2)
+        plan.spmv(xd, yd)
+        torch.cuda.synchronize()
+        plan_io = {"file_bytes": os.path.getsize(path), "save_ms": save_ms, "load_ms": load_ms,
+                   "x_spmv_loaded": load_ms / ms_per_step, "bit_identical": bool(torch.equal(y2, yd))}
+        loaded.close()
+        os.unlink(path)
+        os.rmdir(d)
+
     # ---- e2e through the public host entry (pinned host x, y copied every step)
     xh = torch.from_numpy(x).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -376,7 +398,7 @@ def run_ehyb(args):
             "roofline": roof, "csr_baseline": csr,
             "preprocessing": {"plan_ms": plan_ms, "partition_ms": info["partition_ms"],
                               "reorder_ms": info["reorder_ms"], "upload_ms": info["upload_ms"],
-                              "x_spmv": plan_ms / ms_per_step},
+                              "x_spmv": plan_ms / ms_per_step, "plan_file": plan_io},
             "e2e": e2e, "gpu_launches": (1 if fused else 2) * args.steps, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, x, args.cpu_seconds)
@@ -559,6 +581,7 @@ def main():
     ap.add_argument("--impl", default="ehyb", choices=["ehyb", "reference"])
     ap.add_argument("--workload", default="hex_elast3d_70", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-csr", action="store_true")
+    ap.add_argument("--plan-io", action="store_true", help="also time saving the plan to a file and loading it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--solver", action="store_true", help="time CG / refined CG instead of the SpMV")

@@ -55,7 +55,8 @@ typedef enum {
   EHYB_ERR_UNSUPPORTED = 7,   /* operation not available for this plan (e.g. host-only plan) */
   EHYB_ERR_NOT_CONVERGED = 8, /* iterative solver stopped at max_iter */
   EHYB_ERR_TIMEOUT = 9,       /* a bounded device-side wait ran out; results of that call are invalid */
-  EHYB_ERR_NO_DEVICE = 10     /* no CUDA device */
+  EHYB_ERR_NO_DEVICE = 10,    /* no CUDA device */
+  EHYB_ERR_IO = 11            /* a plan file cannot be written or read, or fails its checksum / structure checks */
 } ehyb_status_t;
 
 typedef enum { EHYB_F64 = 0, EHYB_F32 = 1, EHYB_BF16 = 2 } ehyb_dtype_t;
@@ -269,6 +270,26 @@ ehyb_status_t ehyb_plan_check(ehyb_plan_t plan);
 /* Fill *ex with pointers to host copies of the plan arrays (copied back from the device
  * on first use when the plan did not keep them).  Valid until ehyb_destroy. */
 ehyb_status_t ehyb_plan_export(ehyb_plan_t plan, ehyb_plan_export_t* ex);
+
+/*
+ * Plan files (the preprocessing of Sec. 3.1-3.3 -- partition, reorder, encode -- done once and reused;
+ * the paper weighs its cost against the SpMVs of a solver, Sec. 6).
+ *
+ * ehyb_plan_save writes the plan's partition, permutation and FP64 slab / ER arrays to `path` (read back
+ * from the device when the plan did not keep host copies; synchronises the device).  The file is in the
+ * machine's native byte order with a checksum.  EHYB_ERR_IO when the file cannot be written.
+ *
+ * ehyb_plan_load reads such a file, verifies its checksum and every structural invariant the kernels
+ * index by (permutation, monotone pointers, slice widths, column ranges), then uploads it like
+ * ehyb_plan_create_csr (synchronous).  From `opt` (NULL = defaults) it takes the run-time choices only:
+ * lowp (FP32 / BF16 value copies are made from the stored FP64 values), er_tpr, block_threads, host_only,
+ * num_sms, wait_timeout_ns, keep_host; the partition and encoding come from the file.  A loaded plan
+ * computes bit-identical results to the plan that was saved.  EHYB_ERR_IO when the file is missing,
+ * truncated, of another format version, fails its checksum or its structure checks; EHYB_ERR_TOO_LARGE
+ * when a partition does not fit this device's shared memory.
+ */
+ehyb_status_t ehyb_plan_save(ehyb_plan_t plan, const char* path);
+ehyb_status_t ehyb_plan_load(const char* path, const ehyb_options_t* opt, void* stream, ehyb_plan_t* out);
 
 /*
  * Kernel timing: while enabled, every SpMV call on the plan records a CUDA event pair around

@@ -26,8 +26,8 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 STATUS = {0: "EHYB_OK", 1: "EHYB_ERR_INVALID_ARG", 2: "EHYB_ERR_NOT_SQUARE", 3: "EHYB_ERR_INDEX_RANGE",
           4: "EHYB_ERR_TOO_LARGE", 5: "EHYB_ERR_OOM", 6: "EHYB_ERR_CUDA", 7: "EHYB_ERR_UNSUPPORTED",
-          8: "EHYB_ERR_NOT_CONVERGED", 9: "EHYB_ERR_TIMEOUT", 10: "EHYB_ERR_NO_DEVICE"}
-EHYB_OK, EHYB_ERR_TIMEOUT, EHYB_ERR_NOT_CONVERGED = 0, 9, 8
+          8: "EHYB_ERR_NOT_CONVERGED", 9: "EHYB_ERR_TIMEOUT", 10: "EHYB_ERR_NO_DEVICE", 11: "EHYB_ERR_IO"}
+EHYB_OK, EHYB_ERR_TIMEOUT, EHYB_ERR_NOT_CONVERGED, EHYB_ERR_IO = 0, 9, 8, 11
 
 
 class EhybError(RuntimeError):
@@ -130,6 +130,8 @@ _sig("ehyb_mlp_adam", [_P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float, cty
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
+_sig("ehyb_plan_save", [_P, ctypes.c_char_p])
+_sig("ehyb_plan_load", [ctypes.c_char_p, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)])
 _sig("ehyb_profile_enable", [_P, _I32])
 _sig("ehyb_profile_read", [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)])
 _sig("ehyb_csr_create", [_I64, _I64, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)])
@@ -226,6 +228,15 @@ def ehyb_plan_check(plan):
     return _lib.ehyb_plan_check(plan)
 
 
+def ehyb_plan_save(plan, path: str):
+    return _lib.ehyb_plan_save(plan, os.fsencode(path))
+
+
+def ehyb_plan_load(path: str, opt: Options | None, stream, out: ctypes.c_void_p):
+    return _lib.ehyb_plan_load(os.fsencode(path), ctypes.byref(opt) if opt is not None else None, stream,
+                               ctypes.byref(out))
+
+
 def ehyb_test_fail_allocs_after(count: int):
     _lib.ehyb_test_fail_allocs_after(count)
 
@@ -253,6 +264,21 @@ class Plan:
                                   v.ctypes.data, o, s, self._h)
         _check(st, "ehyb_plan_create_csr")
         self.n = n
+
+    @classmethod
+    def load(cls, path: str, stream=None, **opts):
+        """A plan read from a file written by save() (no partitioning or encoding; opts: run-time choices)."""
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p()
+        o = make_options(**opts)
+        self.host_only = bool(opts.get("host_only", 0))
+        s = None if self.host_only else _stream(stream)
+        _check(ehyb_plan_load(path, o, s, self._h), "ehyb_plan_load")
+        self.n = int(self.info()["n"])
+        return self
+
+    def save(self, path: str):
+        _check(ehyb_plan_save(self._h, path), "ehyb_plan_save")
 
     @property
     def handle(self):

@@ -45,6 +45,26 @@ uint16_t f32_to_bf16_rne(float f) {
   return (uint16_t)((u + bias) >> 16);
 }
 
+void make_lowp_copies(HostPlan& P, int lowp) {
+  const size_t stored = P.ell_val.size(), er_nnz = P.er_val.size(), er_stored = P.er_sval.size();
+  if (lowp == 1) {
+    P.ell_val_f32.resize(stored);
+    P.er_val_f32.resize(er_nnz);
+    P.er_sval_f32.resize(er_stored);
+    for (size_t k = 0; k < stored; ++k) P.ell_val_f32[k] = (float)P.ell_val[k];
+    for (size_t k = 0; k < er_nnz; ++k) P.er_val_f32[k] = (float)P.er_val[k];
+    for (size_t k = 0; k < er_stored; ++k) P.er_sval_f32[k] = (float)P.er_sval[k];
+  } else if (lowp == 2) {
+    P.ell_val_bf16.resize(stored);
+    P.er_val_bf16.resize(er_nnz);
+    P.er_sval_bf16.resize(er_stored);
+    for (size_t k = 0; k < stored; ++k) P.ell_val_bf16[k] = f32_to_bf16_rne((float)P.ell_val[k]);
+    for (size_t k = 0; k < er_nnz; ++k) P.er_val_bf16[k] = f32_to_bf16_rne((float)P.er_val[k]);
+    for (size_t k = 0; k < er_stored; ++k) P.er_sval_bf16[k] = f32_to_bf16_rne((float)P.er_sval[k]);
+  }
+}
+
+
 // ---------------------------------------------------------------- graph
 
 // pattern of A + A^T without the diagonal, each list sorted and duplicate-free
@@ -397,22 +417,7 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     P.row_ell_count[(size_t)r] = (int32_t)j;
     P.ell_nnz += j;
   }
-  if (prm.lowp == 1) {
-    P.ell_val_f32.resize((size_t)stored);
-    P.er_val_f32.resize((size_t)er_nnz);
-    P.er_sval_f32.resize((size_t)er_stored);
-    for (int64_t k = 0; k < stored; ++k) P.ell_val_f32[(size_t)k] = (float)P.ell_val[(size_t)k];
-    for (int64_t k = 0; k < er_nnz; ++k) P.er_val_f32[(size_t)k] = (float)P.er_val[(size_t)k];
-    for (int64_t k = 0; k < er_stored; ++k) P.er_sval_f32[(size_t)k] = (float)P.er_sval[(size_t)k];
-  } else if (prm.lowp == 2) {
-    P.ell_val_bf16.resize((size_t)stored);
-    P.er_val_bf16.resize((size_t)er_nnz);
-    P.er_sval_bf16.resize((size_t)er_stored);
-    for (int64_t k = 0; k < stored; ++k) P.ell_val_bf16[(size_t)k] = f32_to_bf16_rne((float)P.ell_val[(size_t)k]);
-    for (int64_t k = 0; k < er_nnz; ++k) P.er_val_bf16[(size_t)k] = f32_to_bf16_rne((float)P.er_val[(size_t)k]);
-    for (int64_t k = 0; k < er_stored; ++k)
-      P.er_sval_bf16[(size_t)k] = f32_to_bf16_rne((float)P.er_sval[(size_t)k]);
-  }
+  make_lowp_copies(P, prm.lowp);
   P.reorder_ms = now_ms() - t1;
   return 0;
 }

@@ -53,6 +53,10 @@ struct HostPlan {
   double partition_ms = 0, reorder_ms = 0;
 };
 
+// FP32 (lowp 1) or BF16 (lowp 2) copies of the FP64 slab and ER values (FP64 -> FP32 -> BF16, round to
+// nearest even at each step); lowp 0 does nothing
+void make_lowp_copies(HostPlan& P, int lowp);
+
 // Eq. 1 and Eq. 2: smallest K >= 1 with n*tau/(K*P) < budget (and at most 2^16 rows so the
 // 16-bit column offset holds); returns VecSize = ceil(n / (K*P)).
 int32_t eq1_slice_rows(int64_t n, int tau, int P, int64_t budget_bytes);
