@@ -4,7 +4,10 @@
 //                     into parts of at most VecSize vertices.  The paper calls ParMETIS; this is an
 //                     in-house greedy graph-growing partitioner (gain = edges into the growing part,
 //                     FIFO among equal gains, the next part seeded next to the previous one at the
-//                     most enclosed free vertex, a breadth-first sweep order as the fallback).
+//                     most enclosed free vertex, a breadth-first sweep order as the fallback), run on
+//                     the supervariable graph (runs of consecutive rows with equal closed
+//                     neighbourhoods merged, weighted by their row count, split only where a part
+//                     fills up).
 //   eq1_slice_rows  : Eq. 1 and Eq. 2 (Sec. 3.3).
 //   build_plan      : Alg. 1 (per-row in-partition / extra-row counts, sort of each partition's rows
 //                     by in-partition count descending, ReorderTable, yIdxER, PositionELL) and
@@ -12,9 +15,13 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
+#include <mutex>
 #include <chrono>
 #include <climits>
 #include <cstring>
+#include <thread>
 
 namespace ehyb {
 
@@ -67,35 +74,161 @@ void make_lowp_copies(HostPlan& P, int lowp) {
 
 // ---------------------------------------------------------------- graph
 
-// pattern of A + A^T without the diagonal, each list sorted and duplicate-free
-static void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, std::vector<int64_t>& xadj,
+// splitmix64 finaliser: a well-mixed 64-bit hash of x
+static inline uint64_t mix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// f(lo, hi) on `threads` contiguous pieces of [0, count), in parallel (in the caller when threads <= 1)
+template <typename F>
+static void parallel_for(int64_t count, int threads, F&& f, int64_t grain = 4096) {
+  const int64_t t = std::min<int64_t>(threads, (count + grain - 1) / grain);
+  if (t <= 1) {
+    f((int64_t)0, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve((size_t)t);
+  for (int64_t k = 0; k < t; ++k) th.emplace_back([&, k]() { f(count * k / t, count * (k + 1) / t); });
+  for (auto& x : th) x.join();
+}
+
+int planner_threads(int requested) {
+  if (requested > 0) return requested;
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(32u, hw));
+}
+
+// Graph of A for the partitioner: pattern of A + A^T without the diagonal, each list sorted and
+// duplicate-free.  The rows' own sorted lists are built in parallel; when the pattern is symmetric
+// (every FEM matrix) they already are the answer, otherwise the transpose is merged in.
+static void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& xadj,
                           std::vector<int32_t>& adj) {
-  std::vector<int64_t> start(n + 1, 0);
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-      int32_t c = col[k];
-      if (c != i) { ++start[i + 1]; ++start[(int64_t)c + 1]; }
+  std::vector<int64_t> len((size_t)n + 1, 0);
+  std::unique_ptr<int32_t[]> tmp(new int32_t[(size_t)(n > 0 ? rp[n] : 0) + 1]);  // every used slot is written
+  parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      int32_t* b = tmp.get() + rp[i];
+      int64_t m = 0;
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+        if (col[k] != i) b[m++] = col[k];
+      std::sort(b, b + m);
+      len[(size_t)i + 1] = std::unique(b, b + m) - b;
     }
-  for (int64_t i = 0; i < n; ++i) start[i + 1] += start[i];
-  adj.resize((size_t)start[n]);
+  });
+  // the pattern is symmetric when the multiset of its edges (i, c) equals that of (c, i): compared
+  // through two order-independent 64-bit hash sums (a mismatch proves asymmetry; a false match is a
+  // 2^-64 event and would only leave out some edges of the partitioner's heuristic graph)
+  uint64_t fwd = 0, bwd = 0;
+  {
+    std::mutex mu;
+    parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+      uint64_t f = 0, b = 0;
+      for (int64_t i = lo; i < hi; ++i)
+        for (int64_t k = 0; k < len[(size_t)i + 1]; ++k) {
+          const uint64_t c = (uint64_t)tmp[(size_t)(rp[i] + k)];
+          f += mix64(((uint64_t)i << 32) | c);
+          b += mix64((c << 32) | (uint64_t)i);
+        }
+      std::lock_guard<std::mutex> g(mu);
+      fwd += f;
+      bwd += b;
+    });
+  }
+  const bool symmetric = fwd == bwd;
+  if (symmetric) {
+    xadj.assign((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) xadj[(size_t)i + 1] = xadj[(size_t)i] + len[(size_t)i + 1];
+    adj.resize((size_t)xadj[(size_t)n]);
+    parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i)
+        std::copy(tmp.get() + rp[i], tmp.get() + rp[i] + len[(size_t)i + 1], adj.data() + xadj[(size_t)i]);
+    });
+    return;
+  }
+  // general pattern: every edge in both directions, then sort and deduplicate each list
+  std::vector<int64_t> start((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = 0; k < len[(size_t)i + 1]; ++k) {
+      ++start[(size_t)i + 1];
+      ++start[(size_t)tmp[(size_t)(rp[i] + k)] + 1];
+    }
+  for (int64_t i = 0; i < n; ++i) start[(size_t)i + 1] += start[(size_t)i];
+  adj.resize((size_t)start[(size_t)n]);
   std::vector<int64_t> fill(start.begin(), start.end() - 1);
   for (int64_t i = 0; i < n; ++i)
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-      int32_t c = col[k];
-      if (c != i) { adj[(size_t)fill[i]++] = c; adj[(size_t)fill[c]++] = (int32_t)i; }
+    for (int64_t k = 0; k < len[(size_t)i + 1]; ++k) {
+      const int32_t c = tmp[(size_t)(rp[i] + k)];
+      adj[(size_t)fill[(size_t)i]++] = c;
+      adj[(size_t)fill[(size_t)c]++] = (int32_t)i;
     }
+  std::vector<int64_t> ulen((size_t)n + 1, 0);
+  parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      int32_t* b = adj.data() + start[(size_t)i];
+      int32_t* e = adj.data() + start[(size_t)i + 1];
+      std::sort(b, e);
+      ulen[(size_t)i + 1] = std::unique(b, e) - b;
+    }
+  });
   xadj.assign((size_t)n + 1, 0);
-  int64_t w = 0;
+  for (int64_t i = 0; i < n; ++i) xadj[(size_t)i + 1] = xadj[(size_t)i] + ulen[(size_t)i + 1];
+  std::vector<int32_t> out((size_t)xadj[(size_t)n]);
+  parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      std::copy(adj.data() + start[(size_t)i], adj.data() + start[(size_t)i] + ulen[(size_t)i + 1],
+                out.data() + xadj[(size_t)i]);
+  });
+  adj.swap(out);
+}
+
+// Supervariables: maximal runs of consecutive rows whose closed neighbourhoods (the row itself plus its
+// neighbours) coincide -- the dofs of one node of a vector-valued FEM matrix, which are numbered
+// together.  sv_of[i] numbers the runs in row order; run v is rows first[v] .. first[v+1]-1.  Returns
+// the count (n when no two consecutive rows match).
+static int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int threads,
+                              std::vector<int32_t>& sv_of, std::vector<int64_t>& first) {
+  std::vector<uint64_t> key((size_t)n);
+  parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      uint64_t h = mix64((uint64_t)i);  // order-independent hash of the closed neighbourhood
+      for (int64_t e = xadj[(size_t)i]; e < xadj[(size_t)i + 1]; ++e) h += mix64((uint64_t)adj[(size_t)e]);
+      key[(size_t)i] = h;
+    }
+  });
+  // closed neighbourhoods of a and b are equal: same degree, b in N(a), and N(a) \ {b} == N(b) \ {a}
+  auto same = [&](int32_t a, int32_t b) {
+    const int64_t da = xadj[(size_t)a + 1] - xadj[(size_t)a], db = xadj[(size_t)b + 1] - xadj[(size_t)b];
+    if (da != db) return false;
+    const int32_t* pa = adj.data() + xadj[(size_t)a];
+    const int32_t* pb = adj.data() + xadj[(size_t)b];
+    if (!std::binary_search(pa, pa + da, b)) return false;
+    int64_t i = 0, j = 0;
+    while (i < da || j < db) {
+      if (i < da && pa[i] == b) { ++i; continue; }
+      if (j < db && pb[j] == a) { ++j; continue; }
+      if (i >= da || j >= db || pa[i] != pb[j]) return false;
+      ++i;
+      ++j;
+    }
+    return true;
+  };
+  sv_of.assign((size_t)n, 0);
+  first.clear();
+  first.reserve((size_t)n + 1);
+  int64_t nsv = 0;
   for (int64_t i = 0; i < n; ++i) {
-    int32_t* b = adj.data() + start[i];
-    int32_t* e = adj.data() + start[i + 1];
-    std::sort(b, e);
-    int64_t len = std::unique(b, e) - b;
-    if (w != start[i]) std::memmove(adj.data() + w, b, (size_t)len * sizeof(int32_t));
-    w += len;
-    xadj[(size_t)i + 1] = w;
+    if (i == 0 || key[(size_t)i] != key[(size_t)i - 1] || !same((int32_t)first.back(), (int32_t)i)) {
+      first.push_back(i);
+      ++nsv;
+    }
+    sv_of[(size_t)i] = (int32_t)(nsv - 1);
   }
-  adj.resize((size_t)w);
+  first.push_back(n);
+  return nsv;
 }
 
 // breadth-first order over every component; the first component starts at `s`
@@ -124,96 +257,163 @@ static int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std:
   return first_size;
 }
 
-// max-priority bucket queue with FIFO order inside a bucket and lazy deletion
-struct BucketQueue {
-  std::vector<std::vector<int32_t>> b;
-  std::vector<size_t> head;
-  int top = -1, used = -1;
-  explicit BucketQueue(int nkeys) : b((size_t)nkeys), head((size_t)nkeys, 0) {}
-  void push(int32_t v, int key) {
-    b[(size_t)key].push_back(v);
-    if (key > top) top = key;
-    if (key > used) used = key;
+// Max-gain queue of free vertices: one FIFO list per gain value, each vertex in at most one list; a
+// vertex whose gain rises moves to the tail of its new list, so among equal gains the one that reached
+// that gain first leaves first.
+struct GainQueue {
+  std::vector<int32_t> head, tail;       // per gain
+  std::vector<int32_t> next, prev, key;  // per vertex; key -1 = not queued
+  std::vector<int32_t> queued;           // vertices queued since the last clear
+  int top = -1;
+  GainQueue(int64_t nv, int nkeys)
+      : head((size_t)nkeys, -1), tail((size_t)nkeys, -1), next((size_t)nv, -1), prev((size_t)nv, -1),
+        key((size_t)nv, -1) {}
+  void unlink(int32_t v) {
+    const int k = key[(size_t)v];
+    if (prev[(size_t)v] >= 0) next[(size_t)prev[(size_t)v]] = next[(size_t)v];
+    else head[(size_t)k] = next[(size_t)v];
+    if (next[(size_t)v] >= 0) prev[(size_t)next[(size_t)v]] = prev[(size_t)v];
+    else tail[(size_t)k] = prev[(size_t)v];
+    key[(size_t)v] = -1;
   }
-  bool pop(int32_t& v, int& key) {
-    while (top >= 0) {
-      size_t t = (size_t)top;
-      if (head[t] < b[t].size()) { v = b[t][head[t]++]; key = top; return true; }
-      --top;
-    }
-    return false;
+  // (re)queue v with gain k at the tail of that gain's list
+  void raise(int32_t v, int k) {
+    if (key[(size_t)v] >= 0) unlink(v);
+    else queued.push_back(v);
+    key[(size_t)v] = k;
+    next[(size_t)v] = -1;
+    prev[(size_t)v] = tail[(size_t)k];
+    if (tail[(size_t)k] >= 0) next[(size_t)tail[(size_t)k]] = v;
+    else head[(size_t)k] = v;
+    tail[(size_t)k] = v;
+    if (k > top) top = k;
+  }
+  bool pop(int32_t& v) {
+    while (top >= 0 && head[(size_t)top] < 0) --top;
+    if (top < 0) return false;
+    v = head[(size_t)top];
+    unlink(v);
+    return true;
   }
   void clear() {
-    for (int k = 0; k <= used; ++k) { b[(size_t)k].clear(); head[(size_t)k] = 0; }
-    top = used = -1;
+    for (int32_t v : queued)
+      if (key[(size_t)v] >= 0) {
+        head[(size_t)key[(size_t)v]] = tail[(size_t)key[(size_t)v]] = -1;
+        key[(size_t)v] = -1;
+      }
+    queued.clear();
+    top = -1;
   }
 };
 
-int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_t cap, std::vector<int32_t>& part) {
+int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_t cap, std::vector<int32_t>& part,
+                        int threads) {
   part.assign((size_t)n, -1);
   if (n == 0) return 0;
   if (cap < 1) cap = 1;
+  threads = planner_threads(threads);
   std::vector<int64_t> xadj;
   std::vector<int32_t> adj;
-  sym_adjacency(n, rp, col, xadj, adj);
+  sym_adjacency(n, rp, col, threads, xadj, adj);
+
+  // grow on the supervariable graph: vertex weight = rows of the supervariable; an edge wherever two
+  // supervariables' rows are adjacent
+  std::vector<int32_t> sv_of;
+  std::vector<int64_t> first;
+  const int64_t nv = supervariables(n, xadj, adj, threads, sv_of, first);
+  std::vector<int64_t> gx;
+  std::vector<int32_t> ga;
+  if (nv < n) {
+    std::vector<int64_t> glen((size_t)nv + 1, 0);
+    std::vector<std::vector<int32_t>> lists((size_t)nv);
+    parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
+      for (int64_t v = lo; v < hi; ++v) {
+        const int64_t r = first[(size_t)v];  // the rows of a supervariable share their closed neighbourhood
+        std::vector<int32_t>& l = lists[(size_t)v];
+        for (int64_t e = xadj[(size_t)r]; e < xadj[(size_t)r + 1]; ++e) {
+          const int32_t u = sv_of[(size_t)adj[(size_t)e]];
+          if (u != v) l.push_back(u);
+        }
+        std::sort(l.begin(), l.end());
+        l.erase(std::unique(l.begin(), l.end()), l.end());
+        glen[(size_t)v + 1] = (int64_t)l.size();
+      }
+    });
+    gx.assign((size_t)nv + 1, 0);
+    for (int64_t v = 0; v < nv; ++v) gx[(size_t)v + 1] = gx[(size_t)v] + glen[(size_t)v + 1];
+    ga.resize((size_t)gx[(size_t)nv]);
+    for (int64_t v = 0; v < nv; ++v) std::copy(lists[(size_t)v].begin(), lists[(size_t)v].end(), ga.begin() + gx[(size_t)v]);
+    std::vector<int64_t>().swap(xadj);
+    std::vector<int32_t>().swap(adj);
+  } else {
+    gx.swap(xadj);
+    ga.swap(adj);
+  }
+
   // pseudo-peripheral start: the last vertex reached by a breadth-first search from vertex 0
   std::vector<int32_t> order;
-  int64_t comp0 = bfs_order(n, xadj, adj, 0, order);
+  int64_t comp0 = bfs_order(nv, gx, ga, 0, order);
   int32_t start = order[(size_t)comp0 - 1];
-  bfs_order(n, xadj, adj, start, order);
+  bfs_order(nv, gx, ga, start, order);
 
   int64_t maxdeg = 0;
-  for (int64_t i = 0; i < n; ++i) maxdeg = std::max(maxdeg, xadj[(size_t)i + 1] - xadj[(size_t)i]);
-  BucketQueue q((int)maxdeg + 2);
-  std::vector<int32_t> conn((size_t)n, 0), touched, members, stamp((size_t)n, -1);
+  for (int64_t v = 0; v < nv; ++v) maxdeg = std::max(maxdeg, gx[(size_t)v + 1] - gx[(size_t)v]);
+  GainQueue q(nv, (int)maxdeg + 2);
+  std::vector<int32_t> conn((size_t)nv, 0), touched, members, stamp((size_t)nv, -1);
+  std::vector<int64_t> next_row(first.begin(), first.end() - 1);  // first unassigned row of each vertex
+  std::vector<char> done((size_t)nv, 0);
   int64_t cursor = 0, assigned = 0;
   auto next_free = [&]() -> int32_t {
-    while (cursor < n && part[(size_t)order[(size_t)cursor]] != -1) ++cursor;
-    return cursor < n ? order[(size_t)cursor] : -1;
+    while (cursor < nv && done[(size_t)order[(size_t)cursor]]) ++cursor;
+    return cursor < nv ? order[(size_t)cursor] : -1;
   };
   int32_t p = 0, seed = start;
   while (assigned < n) {
-    if (seed < 0 || part[(size_t)seed] != -1) seed = next_free();
+    if (seed < 0 || done[(size_t)seed]) seed = next_free();
     members.clear();
     int32_t size = 0;
+    // take as many of v's remaining rows as the part holds
     auto add = [&](int32_t v) {
-      part[(size_t)v] = p;
-      ++size;
-      ++assigned;
+      const int64_t left = first[(size_t)v + 1] - next_row[(size_t)v];
+      const int64_t take = std::min<int64_t>(left, (int64_t)cap - size);
+      for (int64_t k = 0; k < take; ++k) part[(size_t)next_row[(size_t)v]++] = p;
+      size += (int32_t)take;
+      assigned += take;
+      if (take < left) return;
+      done[(size_t)v] = 1;
       members.push_back(v);
-      for (int64_t e = xadj[(size_t)v]; e < xadj[(size_t)v + 1]; ++e) {
-        int32_t u = adj[(size_t)e];
-        if (part[(size_t)u] != -1) continue;
+      for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
+        int32_t u = ga[(size_t)e];
+        if (done[(size_t)u]) continue;
         if (conn[(size_t)u] == 0) touched.push_back(u);
-        q.push(u, ++conn[(size_t)u]);
+        q.raise(u, ++conn[(size_t)u]);
       }
     };
     add(seed);
     while (size < cap && assigned < n) {
       int32_t v = -1;
-      int key = 0;
-      bool got = false;
-      while (q.pop(v, key))
-        if (part[(size_t)v] == -1 && conn[(size_t)v] == key) { got = true; break; }
-      if (!got) v = next_free();  // frontier exhausted: continue this part elsewhere in sweep order
+      if (!q.pop(v)) v = next_free();  // frontier exhausted: continue this part elsewhere in sweep order
       if (v < 0) break;
       add(v);
     }
     for (int32_t u : touched) conn[(size_t)u] = 0;
     touched.clear();
     q.clear();
-    // next seed: the free neighbour of this part with the most already-assigned neighbours
+    // next seed: the free neighbour of this part with the most already-assigned neighbours (a vertex
+    // split by the full part stays free and joins whichever part reaches it)
     seed = -1;
-    int64_t best = -1;
-    for (int32_t v : members)
-      for (int64_t e = xadj[(size_t)v]; e < xadj[(size_t)v + 1]; ++e) {
-        int32_t u = adj[(size_t)e];
-        if (part[(size_t)u] != -1 || stamp[(size_t)u] == p) continue;
-        stamp[(size_t)u] = p;
-        int64_t a = 0;
-        for (int64_t f = xadj[(size_t)u]; f < xadj[(size_t)u + 1]; ++f) a += part[(size_t)adj[(size_t)f]] != -1;
-        if (a > best) { best = a; seed = u; }
-      }
+    {
+      int64_t best = -1;
+      for (int32_t v : members)
+        for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
+          int32_t u = ga[(size_t)e];
+          if (done[(size_t)u] || stamp[(size_t)u] == p) continue;
+          stamp[(size_t)u] = p;
+          int64_t a = 0;
+          for (int64_t f = gx[(size_t)u]; f < gx[(size_t)u + 1]; ++f) a += done[(size_t)ga[(size_t)f]] != 0;
+          if (a > best) { best = a; seed = u; }
+        }
+    }
     ++p;
   }
   return p;
@@ -225,6 +425,7 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   const double t0 = now_ms();
   const int64_t n = prm.n;
   const int64_t nnz = n > 0 ? rp[n] : 0;
+  const int T = planner_threads(prm.threads);
   const int tpr = prm.ell_tpr;
   const int rps = 32 / tpr;  // rows per 32-lane slice
   P.n = n;
@@ -239,7 +440,7 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     part.assign(prm.part_vec, prm.part_vec + n);
     for (int64_t i = 0; i < n; ++i) nparts = std::max(nparts, part[(size_t)i] + 1);
   } else {
-    nparts = partition_graph(n, rp, col, prm.slice_rows, part);
+    nparts = partition_graph(n, rp, col, prm.slice_rows, part, prm.threads);
   }
   P.nparts = nparts;
   const double t1 = now_ms();
@@ -248,16 +449,18 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   // S_array1 / S_array2: in-partition (slab) and extra-row entry counts of every row
   const int64_t cap = prm.ell_width_cap > 0 ? prm.ell_width_cap : INT64_MAX;
   std::vector<int32_t> cin((size_t)n), cer((size_t)n);
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t a = 0, b = 0;
-    const int32_t pi = part[(size_t)i];
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-      if (part[(size_t)col[k]] == pi && a < cap) ++a;
-      else ++b;
+  parallel_for(n, T, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      int64_t a = 0, b = 0;
+      const int32_t pi = part[(size_t)i];
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if (part[(size_t)col[k]] == pi && a < cap) ++a;
+        else ++b;
+      }
+      cin[(size_t)i] = (int32_t)a;
+      cer[(size_t)i] = (int32_t)b;
     }
-    cin[(size_t)i] = (int32_t)a;
-    cer[(size_t)i] = (int32_t)b;
-  }
+  });
 
   // partition boundaries and the per-partition sort (descending in-partition count, stable)
   P.part_ptr.assign((size_t)nparts + 1, 0);
@@ -269,19 +472,24 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     for (int64_t i = 0; i < n; ++i) P.new_to_old[(size_t)fill[(size_t)part[(size_t)i]]++] = (int32_t)i;
   }
   P.max_part_rows = 0;
-  for (int32_t p = 0; p < nparts; ++p) {
-    auto b = P.new_to_old.begin() + P.part_ptr[(size_t)p], e = P.new_to_old.begin() + P.part_ptr[(size_t)p + 1];
-    // Alg. 1 sorts by in-partition count, descending; ties go to the larger extra-row count first,
-    // which keeps the extra-row widths of a 32-row slice close together (less slice padding)
-    std::stable_sort(b, e, [&](int32_t a, int32_t c) {
-      if (cin[(size_t)a] != cin[(size_t)c]) return cin[(size_t)a] > cin[(size_t)c];
-      return cer[(size_t)a] > cer[(size_t)c];
-    });
+  for (int32_t p = 0; p < nparts; ++p)
     P.max_part_rows = std::max(P.max_part_rows, P.part_ptr[(size_t)p + 1] - P.part_ptr[(size_t)p]);
-  }
   if (P.max_part_rows > 65536) return 4;  // the 16-bit column offset would overflow
+  parallel_for(nparts, T, [&](int64_t lo, int64_t hi) {
+    for (int64_t p = lo; p < hi; ++p) {
+      auto b = P.new_to_old.begin() + P.part_ptr[(size_t)p], e = P.new_to_old.begin() + P.part_ptr[(size_t)p + 1];
+      // Alg. 1 sorts by in-partition count, descending; ties go to the larger extra-row count first,
+      // which keeps the extra-row widths of a 32-row slice close together (less slice padding)
+      std::stable_sort(b, e, [&](int32_t a, int32_t c) {
+        if (cin[(size_t)a] != cin[(size_t)c]) return cin[(size_t)a] > cin[(size_t)c];
+        return cer[(size_t)a] > cer[(size_t)c];
+      });
+    }
+  }, 1);
   P.old_to_new.resize((size_t)n);
-  for (int64_t r = 0; r < n; ++r) P.old_to_new[(size_t)P.new_to_old[(size_t)r]] = (int32_t)r;
+  parallel_for(n, T, [&](int64_t lo, int64_t hi) {
+    for (int64_t r = lo; r < hi; ++r) P.old_to_new[(size_t)P.new_to_old[(size_t)r]] = (int32_t)r;
+  });
 
   // slices (rps rows each, never straddling partitions) and PositionELL
   P.slice_ptr.assign((size_t)nparts + 1, 0);
@@ -384,39 +592,46 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   std::vector<int32_t> part_of_new((size_t)nparts > 0 ? (size_t)n : 0);
   for (int32_t p = 0; p < nparts; ++p)
     for (int32_t r = P.part_ptr[(size_t)p]; r < P.part_ptr[(size_t)p + 1]; ++r) part_of_new[(size_t)r] = p;
-  for (int64_t r = 0; r < n; ++r) {
-    const int32_t i = P.new_to_old[(size_t)r];
-    const int32_t p = part_of_new[(size_t)r];
-    const int32_t pb = P.part_ptr[(size_t)p];
-    const int32_t l = (int32_t)r - pb;
-    const int32_t sl = P.slice_ptr[(size_t)p] + l / rps;
-    const int64_t base = P.slice_pos[(size_t)sl];
-    const int64_t ebase = P.er_slice_pos[(size_t)sl];
-    const int32_t lane0 = (l % rps) * tpr;
-    int64_t j = 0, je = 0;
-    int64_t eo = line_of[(size_t)r] >= 0 ? P.er_ptr[(size_t)line_of[(size_t)r]] : -1;
-    for (int64_t k = rp[i]; k < rp[(int64_t)i + 1]; ++k) {
-      const int32_t c = col[k];
-      if (part[(size_t)c] == part[(size_t)i] && j < cap) {
-        const int64_t pos = base + 32 * (j / tpr) + lane0 + (int32_t)(j % tpr);
-        P.ell_col[(size_t)pos] = (uint16_t)(P.old_to_new[(size_t)c] - pb);
-        P.ell_val[(size_t)pos] = val[k];
-        ++j;
-      } else if (P.er_layout == 0) {
-        const int64_t pos = ebase + 32 * (je / tpr) + lane0 + (int32_t)(je % tpr);
-        P.er_scol[(size_t)pos] = P.old_to_new[(size_t)c];
-        P.er_scol_old[(size_t)pos] = c;
-        P.er_sval[(size_t)pos] = val[k];
-        ++je;
-      } else {
-        P.er_col[(size_t)eo] = P.old_to_new[(size_t)c];
-        P.er_val[(size_t)eo] = val[k];
-        ++eo;
+  std::vector<int64_t> ell_part((size_t)T + 1, 0);
+  std::atomic<int> piece{0};
+  parallel_for(n, T, [&](int64_t lo, int64_t hi) {
+    int64_t ell_sum = 0;
+    for (int64_t r = lo; r < hi; ++r) {
+      const int32_t i = P.new_to_old[(size_t)r];
+      const int32_t p = part_of_new[(size_t)r];
+      const int32_t pb = P.part_ptr[(size_t)p];
+      const int32_t l = (int32_t)r - pb;
+      const int32_t sl = P.slice_ptr[(size_t)p] + l / rps;
+      const int64_t base = P.slice_pos[(size_t)sl];
+      const int64_t ebase = P.er_slice_pos[(size_t)sl];
+      const int32_t lane0 = (l % rps) * tpr;
+      int64_t j = 0, je = 0;
+      int64_t eo = line_of[(size_t)r] >= 0 ? P.er_ptr[(size_t)line_of[(size_t)r]] : -1;
+      for (int64_t k = rp[i]; k < rp[(int64_t)i + 1]; ++k) {
+        const int32_t c = col[k];
+        if (part[(size_t)c] == part[(size_t)i] && j < cap) {
+          const int64_t pos = base + 32 * (j / tpr) + lane0 + (int32_t)(j % tpr);
+          P.ell_col[(size_t)pos] = (uint16_t)(P.old_to_new[(size_t)c] - pb);
+          P.ell_val[(size_t)pos] = val[k];
+          ++j;
+        } else if (P.er_layout == 0) {
+          const int64_t pos = ebase + 32 * (je / tpr) + lane0 + (int32_t)(je % tpr);
+          P.er_scol[(size_t)pos] = P.old_to_new[(size_t)c];
+          P.er_scol_old[(size_t)pos] = c;
+          P.er_sval[(size_t)pos] = val[k];
+          ++je;
+        } else {
+          P.er_col[(size_t)eo] = P.old_to_new[(size_t)c];
+          P.er_val[(size_t)eo] = val[k];
+          ++eo;
+        }
       }
+      P.row_ell_count[(size_t)r] = (int32_t)j;
+      ell_sum += j;
     }
-    P.row_ell_count[(size_t)r] = (int32_t)j;
-    P.ell_nnz += j;
-  }
+    ell_part[(size_t)piece.fetch_add(1)] = ell_sum;
+  });
+  for (int64_t v : ell_part) P.ell_nnz += v;
   make_lowp_copies(P, prm.lowp);
   P.reorder_ms = now_ms() - t1;
   return 0;

@@ -14,6 +14,7 @@ struct PlanParams {
   int32_t lowp = 0;           // 0 none, 1 fp32, 2 bf16 value copies
   int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR
   const int32_t* part_vec = nullptr;
+  int32_t threads = 0;        // host threads for the parallel phases (0 = the machine's); results do not depend on it
 };
 
 struct HostPlan {
@@ -62,9 +63,13 @@ void make_lowp_copies(HostPlan& P, int lowp);
 int32_t eq1_slice_rows(int64_t n, int tau, int P, int64_t budget_bytes);
 
 // Partition the symmetrised graph of A (pattern of A + A^T, no self loops) into parts of at most
-// `cap` vertices by greedy graph growing; returns the number of parts.
+// `cap` vertices by greedy graph growing; returns the number of parts.  threads: host threads for the
+// parallel phases (0 = the machine's, capped at 32); the result does not depend on it.
 int32_t partition_graph(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t cap,
-                        std::vector<int32_t>& part);
+                        std::vector<int32_t>& part, int threads = 0);
+
+// host threads the planner uses for `requested` (0 = the machine's, at most 32)
+int planner_threads(int requested);
 
 // 0 on success, else an ehyb_status_t code (validation is done by the caller).
 int build_plan(const PlanParams& prm, const int64_t* row_ptr, const int32_t* col, const double* val,

@@ -188,7 +188,9 @@ ehyb_status_t sweep_impl(int64_t n, const int64_t* rp, const int32_t* col, const
       bool dup = false;
       for (int sj = 0; sj < si; ++sj) dup |= slices[sj] == slices[si];
       if (!dup)
-        th.emplace_back([&, si]() { partition_graph(n, rp, col, slices[si], parts[(size_t)si]); });
+        th.emplace_back([&, si]() {
+          partition_graph(n, rp, col, slices[si], parts[(size_t)si], std::max(1, planner_threads(0) / kSlices));
+        });
     }
     for (auto& t : th) t.join();
     for (int si = 0; si < kSlices; ++si)
@@ -222,6 +224,7 @@ ehyb_status_t sweep_impl(int64_t n, const int64_t* rp, const int32_t* col, const
         prm.ell_width_cap = caps[ci];
         prm.ell_tpr = kTprVal[ti];
         prm.part_vec = n > 0 ? parts[(size_t)si].data() : nullptr;
+        prm.threads = 1;  // the configurations themselves are built in parallel
         try {
           rc[(size_t)(g - g0)] = build_plan(prm, rp, col, val, P->host);
         } catch (...) {
