@@ -11,6 +11,7 @@ Contents
   * ``spmv``, ``spmm``, ``cg``, ``cg_refined``, ``spmv_low`` -- ctypes wrappers of
     ``oracle.c`` (plain FP64 C, no FMA contraction).
   * ``mlp``     -- FP64 forward/backward/Adam of the tuner's 16-64-64-4 MLP.
+  * ``fsai``    -- the FSAI preconditioner (per-row dense solves) and textbook preconditioned CG.
   * ``ehyb_format`` -- an independent decoder of the EHYB plan arrays back to
     (row, col, val) triplets, the Eq. 1 / Eq. 2 cache-size rule, the Sec. 3.4
     footprint byte model and the per-row rounding-error bound used by parity tests.
