@@ -87,6 +87,7 @@ typedef struct {
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;
+typedef struct ehyb_precond_s* ehyb_precond_t;
 typedef struct ehyb_csr_s* ehyb_csr_t;
 
 typedef struct {
@@ -235,6 +236,43 @@ ehyb_status_t ehyb_cg(ehyb_plan_t plan, const double* b, double* x, double rtol,
 
 /* r.r of the recursion for iterations 0..count-1 of the last FP64 CG solve (or of the last inner solve). */
 ehyb_status_t ehyb_cg_history(ehyb_plan_t plan, double* hist, int32_t cap, int32_t* count);
+
+/* ---- preconditioned CG (the solver of Sec. 6 with its preconditioner as further EHYB products) ---- */
+
+/*
+ * FSAI preconditioner (factorized sparse approximate inverse of an SPD matrix, Kolotilina and Yeremin) for
+ * the matrix of `plan`: G lower triangular on the pattern of the lower triangle of P A P^T (the plan's
+ * numbering), row r from the dense principal block B[J_r, J_r] = L L^T of its pattern J_r as the solution
+ * of L^T g = e_last, so that (G B G^T)_rr = 1; M^-1 = G^T G.  The CSR arrays (host, caller's numbering,
+ * borrowed for the call) must be the matrix the plan was built from.  G and G^T become two EHYB plans on
+ * the plan's own partition (lowp 1 / 2: their values also stored FP32 / BF16 and applied in FP32).
+ * Synchronous.  Needs a plan with the sliced ER layout (EHYB_ERR_UNSUPPORTED otherwise); for a host-only
+ * plan G is built for inspection (ehyb_precond_export) and cannot be used by ehyb_pcg;
+ * EHYB_ERR_INVALID_ARG when a principal block is not positive definite (A not SPD); EHYB_ERR_TOO_LARGE
+ * when a row of G would have more than 1024 entries.
+ */
+ehyb_status_t ehyb_fsai_create(ehyb_plan_t plan, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                               const double* val, int32_t lowp, void* stream, ehyb_precond_t* out);
+/* entries of G and the host time the setup took (ms) */
+ehyb_status_t ehyb_precond_info(ehyb_precond_t M, int64_t* nnz_g, double* setup_ms);
+/* G in the plan's numbering (host CSR, rows sorted; valid until ehyb_precond_destroy) */
+ehyb_status_t ehyb_precond_export(ehyb_precond_t M, int64_t* n, const int64_t** row_ptr, const int32_t** col,
+                                  const double** val);
+ehyb_status_t ehyb_precond_destroy(ehyb_precond_t M); /* NULL is fine; synchronises the device */
+
+/*
+ * Preconditioned CG on `plan` with M (built for this plan): x (device, caller's numbering) holds x0 on
+ * entry and the solution on return; b likewise.  Stops when the recursive residual ||r_k|| <= rtol ||b||
+ * or after max_iter iterations; info->relres is the true FP64 residual ||b - A x|| / ||b|| of the returned
+ * x.  Five launches per iteration (A p with p.q, the update, G r with r.z, G^T t, the direction), replayed
+ * from CUDA graphs of 16 iterations; alpha and beta stay on the device.  Synchronous.
+ * EHYB_ERR_NOT_CONVERGED at the iteration limit or when p.A p <= 0; EHYB_ERR_INVALID_ARG when M belongs
+ * to another plan.
+ */
+ehyb_status_t ehyb_pcg(ehyb_plan_t plan, ehyb_precond_t M, const double* b, double* x, double rtol, int32_t max_iter,
+                       ehyb_cg_info_t* info, void* stream);
+/* r.r of iterations 0..count-1 of the last ehyb_pcg solve with M */
+ehyb_status_t ehyb_pcg_history(ehyb_precond_t M, double* rr, int32_t cap, int32_t* count);
 
 /* ---- batching: many plans in one persistent launch ---- */
 

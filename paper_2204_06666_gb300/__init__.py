@@ -131,6 +131,12 @@ _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
 _sig("ehyb_plan_save", [_P, ctypes.c_char_p])
+_sig("ehyb_fsai_create", [_P, _I64, _I64, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)])
+_sig("ehyb_precond_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D)])
+_sig("ehyb_precond_export", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)])
+_sig("ehyb_precond_destroy", [_P])
+_sig("ehyb_pcg", [_P, _P, _P, _P, _D, _I32, ctypes.POINTER(CgInfo), _P])
+_sig("ehyb_pcg_history", [_P, _P, _I32, ctypes.POINTER(_I32)])
 _sig("ehyb_plan_load", [ctypes.c_char_p, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)])
 _sig("ehyb_profile_enable", [_P, _I32])
 _sig("ehyb_profile_read", [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)])
@@ -335,6 +341,16 @@ class Plan:
             raise EhybError(st, "ehyb_cg")
         return st, info.as_dict()
 
+    def pcg(self, M: "Fsai", b, x, rtol: float = 1e-10, max_iter: int = 10000, stream=None,
+            raise_not_converged: bool = False):
+        """Preconditioned CG with M (an Fsai of this plan), in place on x (CUDA float64, original numbering)."""
+        info = CgInfo()
+        st = _lib.ehyb_pcg(self._h, M._h, _dev(b, "float64"), _dev(x, "float64"), float(rtol), int(max_iter),
+                           ctypes.byref(info), _stream(stream))
+        if st != 0 and (st != EHYB_ERR_NOT_CONVERGED or raise_not_converged):
+            raise EhybError(st, "ehyb_pcg")
+        return st, info.as_dict()
+
     def cg_history(self, cap: int = 100000) -> np.ndarray:
         h = np.zeros(cap)
         cnt = ctypes.c_int32(0)
@@ -382,6 +398,57 @@ class Plan:
         ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
         _check(_lib.ehyb_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)), "ehyb_profile_read")
         return ms.value, cnt.value
+
+
+class Fsai:
+    """FSAI preconditioner (M^-1 = G^T G) of a plan's matrix A (the same host CSR the plan was built from)."""
+
+    def __init__(self, plan: "Plan", A, lowp: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        self.plan = plan    # keeps the plan alive as long as the preconditioner
+        rp = np.ascontiguousarray(A.row_ptr, np.int64)
+        c = np.ascontiguousarray(A.col, np.int32)
+        v = np.ascontiguousarray(A.val, np.float64)
+        s = None if plan.host_only else _stream(stream)
+        _check(_lib.ehyb_fsai_create(plan.handle, int(A.n), int(rp[-1]) if rp.size else 0, rp.ctypes.data,
+                                     c.ctypes.data, v.ctypes.data, int(lowp), s, ctypes.byref(self._h)),
+               "ehyb_fsai_create")
+
+    def info(self) -> dict:
+        nnz, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
+        _check(_lib.ehyb_precond_info(self._h, ctypes.byref(nnz), ctypes.byref(ms)), "ehyb_precond_info")
+        return {"nnz_g": nnz.value, "setup_ms": ms.value}
+
+    def export(self):
+        """G in the plan's numbering as (row_ptr, col, val) numpy copies."""
+        n, rp, c, v = ctypes.c_int64(0), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(_lib.ehyb_precond_export(self._h, ctypes.byref(n), ctypes.byref(rp), ctypes.byref(c), ctypes.byref(v)),
+               "ehyb_precond_export")
+        row_ptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(ctypes.c_int64)), (n.value + 1,)).copy()
+        nnz = int(row_ptr[-1])
+        if nnz == 0:
+            return row_ptr, np.zeros(0, np.int32), np.zeros(0)
+        col = np.ctypeslib.as_array(ctypes.cast(c, ctypes.POINTER(ctypes.c_int32)), (nnz,)).copy()
+        val = np.ctypeslib.as_array(ctypes.cast(v, ctypes.POINTER(ctypes.c_double)), (nnz,)).copy()
+        return row_ptr, col, val
+
+    def history(self, cap: int = 100000) -> np.ndarray:
+        h = np.zeros(cap)
+        cnt = ctypes.c_int32(0)
+        _check(_lib.ehyb_pcg_history(self._h, h.ctypes.data, cap, ctypes.byref(cnt)), "ehyb_pcg_history")
+        return h[:cnt.value]
+
+    def close(self):
+        if self._h:
+            _check(_lib.ehyb_precond_destroy(self._h), "ehyb_precond_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.ehyb_precond_destroy(self._h)
+        except Exception:
+            pass
 
 
 class CsrBaseline:

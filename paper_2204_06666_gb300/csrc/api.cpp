@@ -126,6 +126,10 @@ struct ehyb_csr_s {
 
 namespace ehyb {
 ehyb_status_t cuda_error_status(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+ehyb_status_t check_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* rp, const int32_t* col,
+                        const double* val) {
+  return validate_csr(n_rows, n_cols, nnz, rp, col, val);
+}
 ehyb_status_t device_query(int* dev, int* sms, int* smem_optin) {
   DeviceInfo d;
   ehyb_status_t st = query_device(d);

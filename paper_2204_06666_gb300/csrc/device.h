@@ -48,13 +48,14 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 
 // Fused slab + ER kernel.  scatter 0: x and y in the plan numbering; 1: x in the plan numbering, y
 // written at new_to_old[r]; 2 (sliced ER layout only, else as 1): x and y both in the caller's numbering,
-// x read through new_to_old while it is staged.
+// x read through new_to_old while it is staged.  The fused dot product is offered with scatter 0 and 2.
 // Fused dot product sum_r y_r * xp_r in FP64 (sliced ER layout only): one partial per partition in
 // part[nparts]; the last block reduces them in a fixed order into *result and resets *arrive (zero).
 struct DotOut {
   double* part;
   int32_t* arrive;
   double* result;
+  int32_t self = 0;  // 1: sum_r y_r * y_r instead of y . xp
 };
 // skip (optional): device flag; the launch returns at once while it is non-zero.
 cudaError_t launch_ehyb_f64(const DevPlan& P, const double* xp, double* y, int scatter, cudaStream_t s,

@@ -179,6 +179,7 @@ struct KArgs {
   uint64_t timeout_ns;
   int32_t inject;
   double* dot_part;       // optional: per-block partial of sum_r y_r * xp_r (fixed summation order)
+  int32_t dot_self;       //   ... of sum_r y_r * y_r instead
   int32_t* dot_arrive;    // optional (with dot_part, one block per partition): arrival counter; the last
   double* dot_result;     //   block reduces the partials into *dot_result and resets the counter
   const int32_t* skip;    // optional: the launch does nothing while *skip != 0 (converged solver)
@@ -346,7 +347,7 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     if (sub == 0 && row < pe) {
       if (SCATTER) y[a.new_to_old[row]] = acc;
       else y[row] = acc;
-      if (dot) dacc = fma((double)acc, (double)xsl[row - pb], dacc);
+      if (dot) dacc = fma((double)acc, a.dot_self ? (double)acc : (double)xsl[row - pb], dacc);
     }
     i = inxt;
     s = nxt;
@@ -443,6 +444,7 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.timeout_ns = P.wait_timeout_ns;
   a.inject = P.inject_wait_fault;
   a.dot_part = nullptr;
+  a.dot_self = 0;
   a.dot_arrive = nullptr;
   a.dot_result = nullptr;
   a.skip = nullptr;

@@ -1,0 +1,395 @@
+// Preconditioned conjugate gradients on an EHYB plan with the FSAI preconditioner M^-1 = G^T G (fsai.cpp):
+// the solver the paper's Sec. 6 motivates, its preconditioner applied as two further EHYB products.
+//
+// All vectors live in the matrix plan's numbering (b and x are permuted once in and once out).  One
+// iteration is five launches:
+//   K1  q = A p on the matrix plan, p . q fused into its epilogue (last block reduces);
+//   K2  alpha = (r.z) / (p.q); x += alpha p; r -= alpha q (FP32 copy of r when G is applied in FP32);
+//       partials of r.r, the last block stores r.r, advances the iteration and raises `done` at
+//       convergence (||r|| <= rtol ||b||), at the iteration limit, or when p.q <= 0;
+//   K3  t = G r on G's plan (the caller's numbering of that plan is the matrix plan's), t . t fused:
+//       t . t = r . G^T G r = r . z, the preconditioned inner product;
+//   K4  z = G^T t on G^T's plan;
+//   K5  beta = (r.z)_new / (r.z)_old; p = z + beta p; the last block moves (r.z)_new into (r.z)_old.
+// alpha, beta and the inner products never leave the device; every reduction has a fixed order, so a
+// solve is bit-reproducible.  Chunks of kChunk iterations are captured once into a CUDA graph and
+// replayed; once `done` is up the remaining launches of a chunk return at once.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "plan_internal.h"
+
+namespace ehyb {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kVB = 608;  // vector-kernel blocks (4 per SM)
+constexpr int kVT = 256;
+constexpr int kChunk = 16;
+
+}  // namespace
+
+struct PcgState {
+  int32_t it, done, converged, breakdown;
+  int32_t arrive_pq, arrive_rz, arrive_rr, arrive_beta;
+  int32_t max_iter, pad[3];
+  double tol2, pq, rz_old, rz_new;
+};
+
+struct PcgWork {
+  int64_t n = 0;
+  int32_t hist_cap = 0, lowp = 0;
+  void* arena = nullptr;
+  double *bp = nullptr, *xp = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *t = nullptr;
+  float *r32 = nullptr, *t32 = nullptr, *z32 = nullptr;
+  double *part = nullptr, *pq_part = nullptr, *rz_part = nullptr, *hist = nullptr;
+  PcgState* st = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+
+void pcg_work_free(PcgWork* w) {
+  if (!w) return;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->cap) cudaStreamDestroy(w->cap);
+  if (w->arena) cudaFree(w->arena);
+  delete w;
+}
+
+namespace {
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// fixed-order block sum; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+  return s;
+}
+
+// fixed-order sum of count partials by one warp (lane-strided, then an xor tree); every lane gets it
+__device__ __forceinline__ double warp_sum(const double* part, int count) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int i = lane; i < count; i += 32) v += part[i];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+  return v;
+}
+
+// r = b - q (and its FP32 copy); partials of r.r
+__global__ void pcg_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ q, double* r,
+                             float* r32, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const double ri = b[i] - q[i];
+    r[i] = ri;
+    if (r32) r32[i] = (float)ri;
+    acc = fma(ri, ri, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// partials of a.a
+__global__ void pcg_norm2(int64_t n, const double* __restrict__ a, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) acc = fma(a[i], a[i], acc);
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// single block: hist[0] = r.r, stopping threshold, counters
+__global__ void pcg_init_finish(const double* part, int np, double tol2, int max_iter, double* hist, PcgState* st) {
+  if (threadIdx.x >= 32) return;
+  const double rr = warp_sum(part, np);
+  if (threadIdx.x == 0) {
+    hist[0] = rr;
+    st->tol2 = tol2;
+    st->it = 0;
+    st->arrive_pq = st->arrive_rz = st->arrive_rr = st->arrive_beta = 0;
+    st->breakdown = 0;
+    st->max_iter = max_iter;
+    st->converged = rr <= tol2 ? 1 : 0;
+    st->done = (st->converged || max_iter <= 0) ? 1 : 0;
+  }
+}
+
+// p = z (from FP64 z or FP32 z32); rz_old = rz_new
+template <typename Z>
+__global__ void pcg_start(int64_t n, const Z* __restrict__ z, double* p, PcgState* st) {
+  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = (double)z[i];
+  if (gtid() == 0) st->rz_old = st->rz_new;
+}
+
+// K2
+__global__ void pcg_update(int64_t n, double* x, const double* __restrict__ p, const double* __restrict__ q,
+                           double* r, float* r32, double* hist, PcgState* st, double* part) {
+  if (st->done) return;
+  __shared__ int last_s;
+  const double pq = st->pq;
+  if (!(pq > 0.0)) {  // A is not positive definite along p (or p vanished): stop
+    if (gtid() == 0) {
+      st->breakdown = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  const double a = st->rz_old / pq;
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    if (r32) r32[i] = (float)ri;
+    acc = fma(ri, ri, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    last_s = atomicAdd(&st->arrive_rr, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_s && threadIdx.x < 32) {
+    __threadfence();
+    const double rr = warp_sum(part, (int)gridDim.x);
+    if (threadIdx.x == 0) {
+      const int k = st->it + 1;
+      hist[k] = rr;
+      st->it = k;
+      st->arrive_rr = 0;
+      if (rr <= st->tol2) {
+        st->converged = 1;
+        st->done = 1;
+      } else if (!(rr < 1e300) || k >= st->max_iter) {
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// K5: p = z + beta p
+template <typename Z>
+__global__ void pcg_pupdate(int64_t n, const Z* __restrict__ z, double* p, PcgState* st) {
+  if (st->done) return;
+  __shared__ int last_s;
+  const double beta = st->rz_new / st->rz_old;
+  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = fma(beta, p[i], (double)z[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_s = atomicAdd(&st->arrive_beta, 1) == (int)gridDim.x - 1;  // every block has read rz_old
+  }
+  __syncthreads();
+  if (last_s && threadIdx.x == 0) {
+    st->rz_old = st->rz_new;
+    st->arrive_beta = 0;
+  }
+}
+
+#define CKP(call)                                                     \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return cuda_error_status(e_, #call);       \
+  } while (0)
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+ehyb_status_t work_get(ehyb_precond_t M, int hist_need, PcgWork** out) {
+  PcgWork* w = M->work;
+  if (w && w->hist_cap >= hist_need) {
+    *out = w;
+    return EHYB_OK;
+  }
+  if (w) {
+    CKP(cudaDeviceSynchronize());
+    pcg_work_free(w);
+    M->work = nullptr;
+  }
+  const int64_t n = M->n;
+  w = new PcgWork();
+  w->n = n;
+  w->lowp = M->lowp;
+  w->hist_cap = hist_need < 1024 ? 1024 : hist_need;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const int nparts = M->plan->dev.nparts;
+  const size_t v64 = al((size_t)(n + 2) * 8), v32 = al((size_t)(n + 4) * 4);
+  const size_t parts = al((size_t)kVB * 8), pp = al((size_t)(nparts + 1) * 8);
+  const size_t hist = al((size_t)(w->hist_cap + 2) * 8), st = al(sizeof(PcgState));
+  const size_t total = 7 * v64 + 3 * v32 + parts + 2 * pp + hist + st;
+  ehyb_status_t s = device_alloc(&w->arena, total);
+  if (s != EHYB_OK) {
+    delete w;
+    return s;
+  }
+  char* b = (char*)w->arena;
+  double** v[] = {&w->bp, &w->xp, &w->r, &w->p, &w->q, &w->z, &w->t};
+  for (double** d : v) { *d = (double*)b; b += v64; }
+  float** f[] = {&w->r32, &w->t32, &w->z32};
+  for (float** d : f) { *d = (float*)b; b += v32; }
+  w->part = (double*)b; b += parts;
+  w->pq_part = (double*)b; b += pp;
+  w->rz_part = (double*)b; b += pp;
+  w->hist = (double*)b; b += hist;
+  w->st = (PcgState*)b;
+  cudaError_t e = cudaMemsetAsync(w->arena, 0, total, 0);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    pcg_work_free(w);
+    return cuda_error_status(e, "pcg workspace");
+  }
+  M->work = w;
+  *out = w;
+  return EHYB_OK;
+}
+
+// t = G r with t.t -> rz_new, then z = G^T t (FP64 or, for an FP32 / BF16 G, on the FP32 copies)
+ehyb_status_t apply_precond(ehyb_precond_t M, PcgWork* w, cudaStream_t s, const int32_t* skip) {
+  DotOut dot{w->rz_part, &w->st->arrive_rz, &w->st->rz_new, 1};
+  if (M->lowp == 0) {
+    CKP(launch_ehyb_f64(M->g->dev, w->r, w->t, 2, s, &dot, skip));
+    CKP(launch_ehyb_f64(M->gt->dev, w->t, w->z, 2, s, nullptr, skip));
+  } else {
+    CKP(launch_ehyb_lowp(M->g->dev, M->lowp, w->r32, w->t32, 2, s, &dot, skip));
+    CKP(launch_ehyb_lowp(M->gt->dev, M->lowp, w->t32, w->z32, 2, s, nullptr, skip));
+  }
+  return EHYB_OK;
+}
+
+ehyb_status_t enqueue_chunk(ehyb_precond_t M, PcgWork* w, cudaStream_t s) {
+  const DevPlan& D = M->plan->dev;
+  const int64_t n = w->n;
+  float* r32 = M->lowp ? w->r32 : nullptr;
+  for (int k = 0; k < kChunk; ++k) {
+    DotOut dot{w->pq_part, &w->st->arrive_pq, &w->st->pq};
+    CKP(launch_ehyb_f64(D, w->p, w->q, 0, s, &dot, &w->st->done));
+    pcg_update<<<kVB, kVT, 0, s>>>(n, w->xp, w->p, w->q, w->r, r32, w->hist, w->st, w->part);
+    ehyb_status_t st = apply_precond(M, w, s, &w->st->done);
+    if (st != EHYB_OK) return st;
+    if (M->lowp == 0) pcg_pupdate<double><<<kVB, kVT, 0, s>>>(n, w->z, w->p, w->st);
+    else pcg_pupdate<float><<<kVB, kVT, 0, s>>>(n, w->z32, w->p, w->st);
+    CKP(cudaGetLastError());
+  }
+  return EHYB_OK;
+}
+
+ehyb_status_t run_chunk(ehyb_precond_t M, PcgWork* w, cudaStream_t s) {
+  if (!w->graph) {
+    cudaGraph_t graph;
+    CKP(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
+    ehyb_status_t st = enqueue_chunk(M, w, w->cap);
+    cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
+    if (st != EHYB_OK) return st;
+    CKP(e);
+    e = cudaGraphInstantiate(&w->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    CKP(e);
+  }
+  CKP(cudaGraphLaunch(w->graph, s));
+  return EHYB_OK;
+}
+
+ehyb_status_t sum_part(PcgWork* w, cudaStream_t s, double* out) {
+  double h[kVB];
+  CKP(cudaMemcpyAsync(h, w->part, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CKP(cudaStreamSynchronize(s));
+  double t = 0.0;
+  for (int i = 0; i < kVB; ++i) t += h[i];
+  *out = t;
+  return EHYB_OK;
+}
+
+}  // namespace
+}  // namespace ehyb
+
+using namespace ehyb;
+
+extern "C" ehyb_status_t ehyb_pcg(ehyb_plan_t P, ehyb_precond_t M, const double* b, double* x, double rtol,
+                                  int32_t max_iter, ehyb_cg_info_t* info, void* stream) {
+  if (!P || !M || !info) return EHYB_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  if (M->plan != P) return EHYB_ERR_INVALID_ARG;  // the preconditioner belongs to another plan
+  if (P->host_only) return EHYB_ERR_UNSUPPORTED;
+  if (!(rtol >= 0.0) || max_iter < 0) return EHYB_ERR_INVALID_ARG;
+  const int64_t n = P->dev.n;
+  const double t0 = now_s();
+  if (n == 0) {
+    info->converged = 1;
+    return EHYB_OK;
+  }
+  if (!b || !x) return EHYB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  PcgWork* w = nullptr;
+  ehyb_status_t st = work_get(M, max_iter + 2, &w);
+  if (st != EHYB_OK) return st;
+  const DevPlan& D = P->dev;
+  float* r32 = M->lowp ? w->r32 : nullptr;
+  CKP(launch_permute_f64(D, 1, b, w->bp, s));
+  CKP(launch_permute_f64(D, 1, x, w->xp, s));
+  pcg_norm2<<<kVB, kVT, 0, s>>>(n, w->bp, w->part);
+  double bb = 0.0;
+  if ((st = sum_part(w, s, &bb)) != EHYB_OK) return st;
+  const double bnorm = bb > 0.0 ? std::sqrt(bb) : 1.0;
+
+  // r = b - A x, z = G^T G r, p = z
+  CKP(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+  pcg_residual<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, r32, w->part);
+  pcg_init_finish<<<1, 32, 0, s>>>(w->part, kVB, rtol * rtol * bnorm * bnorm, max_iter, w->hist, w->st);
+  CKP(cudaGetLastError());
+  if ((st = apply_precond(M, w, s, nullptr)) != EHYB_OK) return st;
+  if (M->lowp == 0) pcg_start<double><<<kVB, kVT, 0, s>>>(n, w->z, w->p, w->st);
+  else pcg_start<float><<<kVB, kVT, 0, s>>>(n, w->z32, w->p, w->st);
+  CKP(cudaGetLastError());
+
+  PcgState h;
+  for (;;) {
+    CKP(cudaMemcpyAsync(&h, w->st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CKP(cudaStreamSynchronize(s));
+    if (h.done) break;
+    if ((st = run_chunk(M, w, s)) != EHYB_OK) return st;
+  }
+  // the true residual of the returned x, in FP64
+  CKP(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+  pcg_residual<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->t, nullptr, w->part);
+  double rr = 0.0;
+  if ((st = sum_part(w, s, &rr)) != EHYB_OK) return st;
+  double rr_rec = 0.0;
+  CKP(cudaMemcpyAsync(&rr_rec, w->hist + h.it, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CKP(launch_permute_f64(D, 0, w->xp, x, s));
+  CKP(cudaStreamSynchronize(s));
+  info->iterations = h.it;
+  info->converged = h.converged;
+  info->relres = std::sqrt(rr) / bnorm;
+  info->relres_recursive = std::sqrt(rr_rec) / bnorm;
+  info->seconds = now_s() - t0;
+  if (h.breakdown) return EHYB_ERR_NOT_CONVERGED;
+  return h.converged ? EHYB_OK : EHYB_ERR_NOT_CONVERGED;
+}
+
+extern "C" ehyb_status_t ehyb_pcg_history(ehyb_precond_t M, double* rr, int32_t count, int32_t* n_out) {
+  if (!M || !n_out || (count > 0 && !rr)) return EHYB_ERR_INVALID_ARG;
+  *n_out = 0;
+  PcgWork* w = M->work;
+  if (!w) return EHYB_OK;
+  PcgState h;
+  CKP(cudaDeviceSynchronize());
+  CKP(cudaMemcpy(&h, w->st, sizeof(h), cudaMemcpyDeviceToHost));
+  const int32_t have = h.it + 1;
+  const int32_t k = count < have ? count : have;
+  if (k > 0) CKP(cudaMemcpy(rr, w->hist, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost));
+  *n_out = k;
+  return EHYB_OK;
+}

@@ -82,20 +82,6 @@ static inline uint64_t mix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-// f(lo, hi) on `threads` contiguous pieces of [0, count), in parallel (in the caller when threads <= 1)
-template <typename F>
-static void parallel_for(int64_t count, int threads, F&& f, int64_t grain = 4096) {
-  const int64_t t = std::min<int64_t>(threads, (count + grain - 1) / grain);
-  if (t <= 1) {
-    f((int64_t)0, count);
-    return;
-  }
-  std::vector<std::thread> th;
-  th.reserve((size_t)t);
-  for (int64_t k = 0; k < t; ++k) th.emplace_back([&, k]() { f(count * k / t, count * (k + 1) / t); });
-  for (auto& x : th) x.join();
-}
-
 int planner_threads(int requested) {
   if (requested > 0) return requested;
   const unsigned hw = std::thread::hardware_concurrency();

@@ -1,7 +1,9 @@
 // Host-side EHYB planner: graph partitioning (Sec. 3.1), the cache-size rule (Eq. 1, Eq. 2),
 // the post-partition reordering (Alg. 1) and the slab / extra-rows encoding (Alg. 2).
 #pragma once
+#include <algorithm>
 #include <cstdint>
+#include <thread>
 #include <vector>
 
 namespace ehyb {
@@ -70,6 +72,21 @@ int32_t partition_graph(int64_t n, const int64_t* row_ptr, const int32_t* col, i
 
 // host threads the planner uses for `requested` (0 = the machine's, at most 32)
 int planner_threads(int requested);
+
+// f(lo, hi) on `threads` contiguous pieces of [0, count), in parallel (in the caller when threads <= 1)
+template <typename F>
+inline void parallel_for(int64_t count, int threads, F&& f, int64_t grain = 4096) {
+  const int64_t t = std::min<int64_t>(threads, (count + grain - 1) / grain);
+  if (t <= 1) {
+    f((int64_t)0, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve((size_t)t);
+  for (int64_t k = 0; k < t; ++k) th.emplace_back([&, k]() { f(count * k / t, count * (k + 1) / t); });
+  for (auto& x : th) x.join();
+}
+
 
 // 0 on success, else an ehyb_status_t code (validation is done by the caller).
 int build_plan(const PlanParams& prm, const int64_t* row_ptr, const int32_t* col, const double* val,

@@ -15,6 +15,11 @@
 namespace ehyb {
 struct CgWork;  // solver workspace, defined in cg.cu
 void cg_work_free(CgWork* w);
+struct PcgWork;  // preconditioned-solver workspace, defined in pcg.cu
+void pcg_work_free(PcgWork* w);
+// the CSR checks of ehyb_plan_create_csr (square, monotone row pointers, columns in range)
+ehyb_status_t check_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* rp, const int32_t* col,
+                        const double* val);
 // records the CUDA error text for ehyb_last_cuda_error and returns EHYB_ERR_CUDA
 ehyb_status_t cuda_error_status(cudaError_t e, const char* what);
 // device allocation through the library's allocation hook (EHYB_ERR_OOM on failure)
@@ -71,3 +76,17 @@ ehyb_status_t learned_choice(int64_t n, const int64_t* rp, const int32_t* col, c
 // mean time of reps ehyb_spmv calls on the plan (allocates its own x and y)
 ehyb_status_t measure_plan_ms(ehyb_plan_t P, int reps, void* stream, double* ms);
 }  // namespace ehyb
+
+// FSAI preconditioner of a plan's matrix (fsai.cpp): G lower triangular in the plan's numbering, applied
+// as M^-1 = G^T G through two EHYB plans whose partitions are the matrix plan's.
+struct ehyb_precond_s {
+  ehyb_plan_t plan = nullptr;  // the matrix plan it belongs to (its numbering)
+  ehyb_plan_t g = nullptr, gt = nullptr;
+  int32_t lowp = 0;
+  int64_t n = 0;
+  std::vector<int64_t> rp;  // G on the host (kept for export)
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  double setup_ms = 0, factor_ms = 0;
+  ehyb::PcgWork* work = nullptr;
+};

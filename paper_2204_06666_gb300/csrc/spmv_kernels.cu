@@ -82,6 +82,7 @@ static cudaError_t set_smem(int bytes) {
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, false, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true>, attr, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, true, true>, attr, bytes))) return e;
   return cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true>, attr, bytes);
 }
 
@@ -129,11 +130,14 @@ static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const 
     a.dot_part = dot->part;
     a.dot_arrive = dot->arrive;
     a.dot_result = dot->result;
+    a.dot_self = dot->self;
   }
   a.skip = skip;
   const bool sl = P.er_layout == 0;
   const V* erv = sl ? erv_sl : erv_csr;
-  if (dot) {  // the fused dot product exists for the sliced layout in the plan numbering (solver use)
+  if (dot && scatter == 2 && sl) {  // caller's numbering with the fused dot (preconditioner SpMVs)
+    launch_pdl<V, X, true, true, true, true>(P, smem, s, a, ev, erv, xp, y);
+  } else if (dot) {  // the fused dot product in the plan numbering (sliced layout, solver use)
     launch_pdl<V, X, false, true, true>(P, smem, s, a, ev, erv, xp, y);
   } else if (scatter == 2 && sl) {  // x in the caller's numbering, permutation fused into the loads
     launch_pdl<V, X, true, true, false, true>(P, smem, s, a, ev, erv, xp, y);
