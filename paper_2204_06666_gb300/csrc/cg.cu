@@ -31,7 +31,7 @@ namespace ehyb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kVB = 608;  // vector-kernel blocks (4 per SM)
+constexpr int kVB = 608;  // vector-kernel blocks (4 per SM; 8 per SM measured slower)
 constexpr int kVT = 256;
 constexpr int kChunk = 16;
 
@@ -156,7 +156,8 @@ template <typename T> __device__ __forceinline__ T& lane_of(typename Vec16<T>::t
 // are 256-byte aligned), scalar tail.  p.q <= 0 means the operator is not positive definite along p:
 // the iteration stops with `breakdown` set and nothing updated.
 template <typename T>
-__global__ void update_kernel(int64_t n, T* x, const T* __restrict__ p, const T* __restrict__ q, T* r,
+__global__ void update_kernel(int64_t n, T* __restrict__ x, const T* __restrict__ p, const T* __restrict__ q,
+                              T* __restrict__ r,
                               double* hist, CgState* st, double* rr_part) {
   if (st->done) return;
   using V = typename Vec16<T>::type;
@@ -229,7 +230,8 @@ __global__ void update_kernel(int64_t n, T* x, const T* __restrict__ p, const T*
 // K3: p = r + beta p (force: run although `done` is up -- the residual-replacement driver completes the
 // iteration whose update raised the flag)
 template <typename T>
-__global__ void pupdate_kernel(int64_t n, T* p, const T* __restrict__ r, const CgState* st, int force = 0) {
+__global__ void pupdate_kernel(int64_t n, T* __restrict__ p, const T* __restrict__ r, const CgState* st,
+                               int force = 0) {
   if (st->done && !force) return;
   if (st->breakdown) return;
   using V = typename Vec16<T>::type;

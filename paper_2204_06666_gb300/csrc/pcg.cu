@@ -2,15 +2,16 @@
 // the solver the paper's Sec. 6 motivates, its preconditioner applied as two further EHYB products.
 //
 // All vectors live in the matrix plan's numbering (b and x are permuted once in and once out).  One
-// iteration is five launches:
+// iteration is four launches:
 //   K1  q = A p on the matrix plan, p . q fused into its epilogue (last block reduces);
 //   K2  alpha = (r.z) / (p.q); x += alpha p; r -= alpha q (FP32 copy of r when G is applied in FP32);
-//       partials of r.r, the last block stores r.r, advances the iteration and raises `done` at
-//       convergence (||r|| <= rtol ||b||), at the iteration limit, or when p.q <= 0;
+//       partials of r.r, the last block stores r.r, keeps r.z as (r.z)_old, advances the iteration and
+//       raises `done` at convergence (||r|| <= rtol ||b||), at the iteration limit, or when p.q <= 0;
 //   K3  t = G r on G's plan (the caller's numbering of that plan is the matrix plan's), t . t fused:
-//       t . t = r . G^T G r = r . z, the preconditioned inner product;
+//       t . t = r . G^T G r = r . z, the new preconditioned inner product;
 //   K4  z = G^T t on G^T's plan;
-//   K5  beta = (r.z)_new / (r.z)_old; p = z + beta p; the last block moves (r.z)_new into (r.z)_old.
+//   K5  p = z + beta p with beta = (r.z)_new / (r.z)_old (a coalesced pass: fusing it into K4's scattered
+//       stores measured slower).
 // alpha, beta and the inner products never leave the device; every reduction has a fixed order, so a
 // solve is bit-reproducible.  Chunks of kChunk iterations are captured once into a CUDA graph and
 // replayed; once `done` is up the remaining launches of a chunk return at once.
@@ -27,7 +28,7 @@ namespace ehyb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kVB = 608;  // vector-kernel blocks (4 per SM)
+constexpr int kVB = 608;  // vector-kernel blocks (4 per SM; 8 per SM measured slower)
 constexpr int kVT = 256;
 constexpr int kChunk = 16;
 
@@ -35,7 +36,7 @@ constexpr int kChunk = 16;
 
 struct PcgState {
   int32_t it, done, converged, breakdown;
-  int32_t arrive_pq, arrive_rz, arrive_rr, arrive_beta;
+  int32_t arrive_pq, arrive_rz, arrive_rr, pad0;
   int32_t max_iter, pad[3];
   double tol2, pq, rz_old, rz_new;
 };
@@ -117,7 +118,7 @@ __global__ void pcg_init_finish(const double* part, int np, double tol2, int max
     hist[0] = rr;
     st->tol2 = tol2;
     st->it = 0;
-    st->arrive_pq = st->arrive_rz = st->arrive_rr = st->arrive_beta = 0;
+    st->arrive_pq = st->arrive_rz = st->arrive_rr = 0;
     st->breakdown = 0;
     st->max_iter = max_iter;
     st->converged = rr <= tol2 ? 1 : 0;
@@ -125,16 +126,16 @@ __global__ void pcg_init_finish(const double* part, int np, double tol2, int max
   }
 }
 
-// p = z (from FP64 z or FP32 z32); rz_old = rz_new
+// p = z (from FP64 z or FP32 z32)
 template <typename Z>
-__global__ void pcg_start(int64_t n, const Z* __restrict__ z, double* p, PcgState* st) {
+__global__ void pcg_start(int64_t n, const Z* __restrict__ z, double* p) {
   for (int64_t i = gtid(); i < n; i += gstride()) p[i] = (double)z[i];
-  if (gtid() == 0) st->rz_old = st->rz_new;
 }
 
-// K2
-__global__ void pcg_update(int64_t n, double* x, const double* __restrict__ p, const double* __restrict__ q,
-                           double* r, float* r32, double* hist, PcgState* st, double* part) {
+// K2 (16-byte accesses; the workspace vectors are 256-byte aligned)
+__global__ void pcg_update(int64_t n, double* __restrict__ x, const double* __restrict__ p,
+                           const double* __restrict__ q, double* __restrict__ r, float* __restrict__ r32, double* hist,
+                           PcgState* st, double* part) {
   if (st->done) return;
   __shared__ int last_s;
   const double pq = st->pq;
@@ -145,9 +146,25 @@ __global__ void pcg_update(int64_t n, double* x, const double* __restrict__ p, c
     }
     return;
   }
-  const double a = st->rz_old / pq;
+  const double a = st->rz_new / pq;
   double acc = 0.0;
-  for (int64_t i = gtid(); i < n; i += gstride()) {
+  const int64_t n2 = n >> 1;
+  for (int64_t j = gtid(); j < n2; j += gstride()) {
+    double2 xv = reinterpret_cast<double2*>(x)[j];
+    const double2 pv = reinterpret_cast<const double2*>(p)[j];
+    const double2 qv = reinterpret_cast<const double2*>(q)[j];
+    double2 rv = reinterpret_cast<double2*>(r)[j];
+    xv.x = fma(a, pv.x, xv.x);
+    xv.y = fma(a, pv.y, xv.y);
+    rv.x = fma(-a, qv.x, rv.x);
+    rv.y = fma(-a, qv.y, rv.y);
+    reinterpret_cast<double2*>(x)[j] = xv;
+    reinterpret_cast<double2*>(r)[j] = rv;
+    if (r32) reinterpret_cast<float2*>(r32)[j] = make_float2((float)rv.x, (float)rv.y);
+    acc = fma(rv.x, rv.x, acc);
+    acc = fma(rv.y, rv.y, acc);
+  }
+  for (int64_t i = 2 * n2 + gtid(); i < n; i += gstride()) {
     x[i] = fma(a, p[i], x[i]);
     const double ri = fma(-a, q[i], r[i]);
     r[i] = ri;
@@ -169,6 +186,7 @@ __global__ void pcg_update(int64_t n, double* x, const double* __restrict__ p, c
       hist[k] = rr;
       st->it = k;
       st->arrive_rr = 0;
+      st->rz_old = st->rz_new;  // every block has read it; K3 overwrites rz_new next
       if (rr <= st->tol2) {
         st->converged = 1;
         st->done = 1;
@@ -179,23 +197,29 @@ __global__ void pcg_update(int64_t n, double* x, const double* __restrict__ p, c
   }
 }
 
-// K5: p = z + beta p
+// K5: p = z + beta p (16-byte accesses)
 template <typename Z>
-__global__ void pcg_pupdate(int64_t n, const Z* __restrict__ z, double* p, PcgState* st) {
+__global__ void pcg_pupdate(int64_t n, const Z* __restrict__ z, double* __restrict__ p, const PcgState* st) {
   if (st->done) return;
-  __shared__ int last_s;
   const double beta = st->rz_new / st->rz_old;
-  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = fma(beta, p[i], (double)z[i]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_s = atomicAdd(&st->arrive_beta, 1) == (int)gridDim.x - 1;  // every block has read rz_old
+  const int64_t n2 = n >> 1;
+  for (int64_t j = gtid(); j < n2; j += gstride()) {
+    double2 pv = reinterpret_cast<double2*>(p)[j];
+    double zx, zy;
+    if (sizeof(Z) == 8) {
+      const double2 zv = reinterpret_cast<const double2*>(z)[j];
+      zx = zv.x;
+      zy = zv.y;
+    } else {
+      const float2 zv = reinterpret_cast<const float2*>(z)[j];
+      zx = zv.x;
+      zy = zv.y;
+    }
+    pv.x = fma(beta, pv.x, zx);
+    pv.y = fma(beta, pv.y, zy);
+    reinterpret_cast<double2*>(p)[j] = pv;
   }
-  __syncthreads();
-  if (last_s && threadIdx.x == 0) {
-    st->rz_old = st->rz_new;
-    st->arrive_beta = 0;
-  }
+  for (int64_t i = 2 * n2 + gtid(); i < n; i += gstride()) p[i] = fma(beta, p[i], (double)z[i]);
 }
 
 #define CKP(call)                                                     \
@@ -256,7 +280,7 @@ ehyb_status_t work_get(ehyb_precond_t M, int hist_need, PcgWork** out) {
   return EHYB_OK;
 }
 
-// t = G r with t.t -> rz_new, then z = G^T t (FP64 or, for an FP32 / BF16 G, on the FP32 copies)
+// t = G r with t.t -> rz_new, then z = G^T t (FP64, or, for an FP32 / BF16 G, on the FP32 copies)
 ehyb_status_t apply_precond(ehyb_precond_t M, PcgWork* w, cudaStream_t s, const int32_t* skip) {
   DotOut dot{w->rz_part, &w->st->arrive_rz, &w->st->rz_new, 1};
   if (M->lowp == 0) {
@@ -350,8 +374,8 @@ extern "C" ehyb_status_t ehyb_pcg(ehyb_plan_t P, ehyb_precond_t M, const double*
   pcg_init_finish<<<1, 32, 0, s>>>(w->part, kVB, rtol * rtol * bnorm * bnorm, max_iter, w->hist, w->st);
   CKP(cudaGetLastError());
   if ((st = apply_precond(M, w, s, nullptr)) != EHYB_OK) return st;
-  if (M->lowp == 0) pcg_start<double><<<kVB, kVT, 0, s>>>(n, w->z, w->p, w->st);
-  else pcg_start<float><<<kVB, kVT, 0, s>>>(n, w->z32, w->p, w->st);
+  if (M->lowp == 0) pcg_start<double><<<kVB, kVT, 0, s>>>(n, w->z, w->p);
+  else pcg_start<float><<<kVB, kVT, 0, s>>>(n, w->z32, w->p);
   CKP(cudaGetLastError());
 
   PcgState h;
