@@ -412,7 +412,9 @@ def run_ehyb(args):
 
 def run_solver(args):
     """Time to a 1e-10 relative residual: FP64 CG vs FP64 refinement around FP32 / BF16 inner CG, both as
-    restarted refinement (refine 1 / 2) and as residual replacement that keeps the direction (refine 3 / 4).
+    restarted refinement (refine 1 / 2) and as residual replacement that keeps the direction (refine 3 / 4),
+    and FSAI-preconditioned CG (G in FP64 / FP32 / BF16; FP64 PCG and FP32 PCG with FP64 residual
+    replacement every 10x or 100x).  The line's value is the FP32 PCG with BF16 G and replacement every 100x.
 
     b = A x* with x* ~ U[-1, 1) (seeded), computed by the library's FP64 SpMV.  Each method solves from
     x0 = 0; one untimed solve, then the median of `--solver-reps` timed solves (host wall clock around
@@ -486,10 +488,34 @@ def run_solver(args):
                      "err_vs_fp64_cg": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)),
                      "ms_per_iteration": 1e3 * statistics.median(times) / max(info["iterations"], 1),
                      "setup_s": setup_s, "nnz_g": M.info()["nnz_g"]}
+        if lowp:   # the same preconditioner in an all-FP32 PCG with FP64 residual replacement every `irt`
+            for irt in (0.1, 0.01):
+                times, res = [], None
+                for rep in range(args.solver_reps + 1):
+                    x = torch.zeros_like(b)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    st, info = P32.pcg_refined(M, b, x, rtol=1e-10, max_iter=args.solver_max_iter, inner_rtol=irt)
+                    dt = time.perf_counter() - t0
+                    if rep > 0:
+                        times.append(dt)
+                    res = (st, info, x)
+                st, info, x = res
+                xh = x.cpu().numpy()
+                out[f"{name}_refined_{irt:g}"] = {
+                    "status": eh.STATUS.get(st, st), "converged": bool(info["converged"]),
+                    "iterations": info["iterations"], "refinements": info["refinements"],
+                    "seconds": statistics.median(times), "relres_fp64": info["relres"],
+                    "err_vs_xstar": float(np.linalg.norm(xh - xstar) / np.linalg.norm(xstar)),
+                    "err_vs_fp64_cg": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)),
+                    "ms_per_iteration": 1e3 * statistics.median(times) / max(info["iterations"], 1),
+                    "setup_s": setup_s, "nnz_g": M.info()["nnz_g"]}
         M.close()
     base = out["fp64_cg"]["seconds"]
-    line = {"metric": "CG time to 1e-10 relative residual (FP64 vs mixed-precision refinement)", "unit": "s",
-            "value": out["replaced_fp32"]["seconds"], "higher_is_better": False, "n_gpus": 1, "dtype": "f64+f32",
+    best = "fsai_pcg_bf16_refined_0.01"
+    line = {"metric": "CG time to 1e-10 relative residual (FP64 CG vs mixed-precision and preconditioned solvers)",
+            "unit": "s", "value": out[best]["seconds"], "method": best,
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64+f32+bf16",
             "data": "synthetic", "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "desc": w["desc"],
                                              "reps": args.solver_reps},
             "methods": out,

@@ -271,7 +271,19 @@ ehyb_status_t ehyb_precond_destroy(ehyb_precond_t M); /* NULL is fine; synchroni
  */
 ehyb_status_t ehyb_pcg(ehyb_plan_t plan, ehyb_precond_t M, const double* b, double* x, double rtol, int32_t max_iter,
                        ehyb_cg_info_t* info, void* stream);
-/* r.r of iterations 0..count-1 of the last ehyb_pcg solve with M */
+/*
+ * Mixed-precision preconditioned CG: one PCG on FP32 vectors that uses A's FP32 / BF16 values (plan built with
+ * opt.lowp = 1 / 2), G's FP32 / BF16 values (M built with lowp = 1 / 2), FP32 accumulation and FP64 inner
+ * products, with FP64 residual replacement: each time the FP32 residual has dropped by inner_rtol (0 = 0.01)
+ * x += s d and r = b - A x are computed in FP64 and the iteration continues on r (direction kept, rescaled).
+ * Stops when ||b - A x|| <= rtol ||b|| (FP64, recomputed at every replacement), after three replacements
+ * without a smaller FP64 residual, or when the iterations reach max_iter.  info->refinements counts the
+ * replacements.  Synchronous.  EHYB_ERR_UNSUPPORTED when the plan or M lacks its low-precision values.
+ */
+ehyb_status_t ehyb_pcg_refined(ehyb_plan_t plan, ehyb_precond_t M, const double* b, double* x, double rtol,
+                               int32_t max_iter, double inner_rtol, ehyb_cg_info_t* info, void* stream);
+/* r.r of iterations 0..count-1 of the last ehyb_pcg solve with M (of the last inner solve for
+ * ehyb_pcg_refined) */
 ehyb_status_t ehyb_pcg_history(ehyb_precond_t M, double* rr, int32_t cap, int32_t* count);
 
 /* ---- batching: many plans in one persistent launch ---- */

@@ -137,6 +137,7 @@ _sig("ehyb_precond_export", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_P), ctype
 _sig("ehyb_precond_destroy", [_P])
 _sig("ehyb_pcg", [_P, _P, _P, _P, _D, _I32, ctypes.POINTER(CgInfo), _P])
 _sig("ehyb_pcg_history", [_P, _P, _I32, ctypes.POINTER(_I32)])
+_sig("ehyb_pcg_refined", [_P, _P, _P, _P, _D, _I32, _D, ctypes.POINTER(CgInfo), _P])
 _sig("ehyb_plan_load", [ctypes.c_char_p, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)])
 _sig("ehyb_profile_enable", [_P, _I32])
 _sig("ehyb_profile_read", [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)])
@@ -349,6 +350,16 @@ class Plan:
                            ctypes.byref(info), _stream(stream))
         if st != 0 and (st != EHYB_ERR_NOT_CONVERGED or raise_not_converged):
             raise EhybError(st, "ehyb_pcg")
+        return st, info.as_dict()
+
+    def pcg_refined(self, M: "Fsai", b, x, rtol: float = 1e-10, max_iter: int = 10000, inner_rtol: float = 0.0,
+                    stream=None, raise_not_converged: bool = False):
+        """FP32 PCG with FP64 residual replacement (the plan and M need their low-precision values)."""
+        info = CgInfo()
+        st = _lib.ehyb_pcg_refined(self._h, M._h, _dev(b, "float64"), _dev(x, "float64"), float(rtol), int(max_iter),
+                                   float(inner_rtol), ctypes.byref(info), _stream(stream))
+        if st != 0 and (st != EHYB_ERR_NOT_CONVERGED or raise_not_converged):
+            raise EhybError(st, "ehyb_pcg_refined")
         return st, info.as_dict()
 
     def cg_history(self, cap: int = 100000) -> np.ndarray:

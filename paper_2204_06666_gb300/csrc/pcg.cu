@@ -15,6 +15,13 @@
 // alpha, beta and the inner products never leave the device; every reduction has a fixed order, so a
 // solve is bit-reproducible.  Chunks of kChunk iterations are captured once into a CUDA graph and
 // replayed; once `done` is up the remaining launches of a chunk return at once.
+//
+// Mixed precision (ehyb_pcg_refined): one PCG that runs on FP32 vectors -- A's FP32 / BF16 values, G's
+// FP32 / BF16 values, FP32 accumulation, FP64 inner products and alpha / beta -- with FP64 residual
+// replacement: the iteration works on d (A d = r / s for the residual r and scale s of the last
+// replacement); whenever its residual has dropped by the factor delta, x += s d in FP64, r = b - A x is
+// recomputed in FP64, the FP32 residual restarts from r / s' and the direction is kept, rescaled by s / s'
+// (and (r.z)_old by (s / s')^2), so the Krylov iteration is not restarted.  Stops when ||b - A x|| <= rtol ||b||.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -46,16 +53,17 @@ struct PcgWork {
   int32_t hist_cap = 0, lowp = 0;
   void* arena = nullptr;
   double *bp = nullptr, *xp = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *t = nullptr;
-  float *r32 = nullptr, *t32 = nullptr, *z32 = nullptr;
+  float *r32 = nullptr, *t32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
   double *part = nullptr, *pq_part = nullptr, *rz_part = nullptr, *hist = nullptr;
   PcgState* st = nullptr;
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr, graph32 = nullptr;
 };
 
 void pcg_work_free(PcgWork* w) {
   if (!w) return;
   if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->graph32) cudaGraphExecDestroy(w->graph32);
   if (w->cap) cudaStreamDestroy(w->cap);
   if (w->arena) cudaFree(w->arena);
   delete w;
@@ -222,6 +230,155 @@ __global__ void pcg_pupdate(int64_t n, const Z* __restrict__ z, double* __restri
   for (int64_t i = 2 * n2 + gtid(); i < n; i += gstride()) p[i] = fma(beta, p[i], (double)z[i]);
 }
 
+// inner start: r32 = r * inv_scale (FP32), d32 = 0; partials of r32.r32
+__global__ void pcg_inner_start(int64_t n, const double* __restrict__ r, double inv_scale, float* __restrict__ r32,
+                                float* __restrict__ d32, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const float ri = (float)(r[i] * inv_scale);
+    r32[i] = ri;
+    d32[i] = 0.0f;
+    acc = fma((double)ri, (double)ri, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// inner K2: d += alpha p; r -= alpha q on FP32 vectors (alpha from FP64 inner products)
+__global__ void pcg_update32(int64_t n, float* __restrict__ d, const float* __restrict__ p,
+                             const float* __restrict__ q, float* __restrict__ r, double* hist, PcgState* st,
+                             double* part) {
+  if (st->done) return;
+  __shared__ int last_s;
+  const double pq = st->pq;
+  if (!(pq > 0.0)) {
+    if (gtid() == 0) {
+      st->breakdown = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  const float a = (float)(st->rz_new / pq);
+  double acc = 0.0;
+  const int64_t n4 = n >> 2;
+  for (int64_t j = gtid(); j < n4; j += gstride()) {
+    float4 dv = reinterpret_cast<float4*>(d)[j];
+    const float4 pv = reinterpret_cast<const float4*>(p)[j];
+    const float4 qv = reinterpret_cast<const float4*>(q)[j];
+    float4 rv = reinterpret_cast<float4*>(r)[j];
+    dv.x = fmaf(a, pv.x, dv.x);
+    dv.y = fmaf(a, pv.y, dv.y);
+    dv.z = fmaf(a, pv.z, dv.z);
+    dv.w = fmaf(a, pv.w, dv.w);
+    rv.x = fmaf(-a, qv.x, rv.x);
+    rv.y = fmaf(-a, qv.y, rv.y);
+    rv.z = fmaf(-a, qv.z, rv.z);
+    rv.w = fmaf(-a, qv.w, rv.w);
+    reinterpret_cast<float4*>(d)[j] = dv;
+    reinterpret_cast<float4*>(r)[j] = rv;
+    acc = fma((double)rv.x, (double)rv.x, acc);
+    acc = fma((double)rv.y, (double)rv.y, acc);
+    acc = fma((double)rv.z, (double)rv.z, acc);
+    acc = fma((double)rv.w, (double)rv.w, acc);
+  }
+  for (int64_t i = 4 * n4 + gtid(); i < n; i += gstride()) {
+    d[i] = fmaf(a, p[i], d[i]);
+    const float ri = fmaf(-a, q[i], r[i]);
+    r[i] = ri;
+    acc = fma((double)ri, (double)ri, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    last_s = atomicAdd(&st->arrive_rr, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_s && threadIdx.x < 32) {
+    __threadfence();
+    const double rr = warp_sum(part, (int)gridDim.x);
+    if (threadIdx.x == 0) {
+      const int k = st->it + 1;
+      hist[k] = rr;
+      st->it = k;
+      st->arrive_rr = 0;
+      st->rz_old = st->rz_new;
+      if (rr <= st->tol2) {
+        st->converged = 1;
+        st->done = 1;
+      } else if (!(rr < 1e30) || k >= st->max_iter) {
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// inner K5: p = z + beta p (FP32)
+__global__ void pcg_pupdate32(int64_t n, const float* __restrict__ z, float* __restrict__ p, const PcgState* st) {
+  if (st->done) return;
+  const float beta = (float)(st->rz_new / st->rz_old);
+  const int64_t n4 = n >> 2;
+  for (int64_t j = gtid(); j < n4; j += gstride()) {
+    float4 pv = reinterpret_cast<float4*>(p)[j];
+    const float4 zv = reinterpret_cast<const float4*>(z)[j];
+    pv.x = fmaf(beta, pv.x, zv.x);
+    pv.y = fmaf(beta, pv.y, zv.y);
+    pv.z = fmaf(beta, pv.z, zv.z);
+    pv.w = fmaf(beta, pv.w, zv.w);
+    reinterpret_cast<float4*>(p)[j] = pv;
+  }
+  for (int64_t i = 4 * n4 + gtid(); i < n; i += gstride()) p[i] = fmaf(beta, p[i], z[i]);
+}
+
+// x += scale * d (the FP64 correction of an outer refinement step)
+__global__ void pcg_correct(int64_t n, double* __restrict__ x, const float* __restrict__ d, double scale) {
+  for (int64_t i = gtid(); i < n; i += gstride()) x[i] = fma(scale, (double)d[i], x[i]);
+}
+
+__global__ void copy_f32(int64_t n, const float* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = gtid(); i < n; i += gstride()) b[i] = a[i];
+}
+
+// residual replacement: r32 = r * inv_scale, d32 = 0, p32 *= ratio; partials of r32.r32
+__global__ void pcg_replace(int64_t n, const double* __restrict__ r, double inv_scale, float ratio,
+                            float* __restrict__ r32, float* __restrict__ d32, float* __restrict__ p32, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const float ri = (float)(r[i] * inv_scale);
+    r32[i] = ri;
+    d32[i] = 0.0f;
+    p32[i] *= ratio;
+    acc = fma((double)ri, (double)ri, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// single block after a replacement: the next segment's threshold and counters; (r.z)_old in the new scale
+__global__ void pcg_replace_finish(const double* part, int np, double delta2, double ratio2, int max_iter,
+                                   double* hist, PcgState* st) {
+  if (threadIdx.x >= 32) return;
+  const double rr = warp_sum(part, np);
+  if (threadIdx.x == 0) {
+    hist[0] = rr;
+    st->tol2 = delta2 * rr;
+    st->it = 0;
+    st->arrive_pq = st->arrive_rz = st->arrive_rr = 0;
+    st->breakdown = 0;
+    st->max_iter = max_iter;
+    st->converged = 0;
+    st->done = max_iter <= 0 ? 1 : 0;
+    st->rz_old *= ratio2;
+  }
+}
+
+// p32 = z32 + beta p32 once, regardless of `done` (completes the iteration a replacement interrupted)
+__global__ void pcg_pupdate32_force(int64_t n, const float* __restrict__ z, float* __restrict__ p,
+                                    const PcgState* st) {
+  const float beta = (float)(st->rz_new / st->rz_old);
+  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = fmaf(beta, p[i], z[i]);
+}
+
 #define CKP(call)                                                     \
   do {                                                                \
     cudaError_t e_ = (call);                                          \
@@ -253,7 +410,7 @@ ehyb_status_t work_get(ehyb_precond_t M, int hist_need, PcgWork** out) {
   const size_t v64 = al((size_t)(n + 2) * 8), v32 = al((size_t)(n + 4) * 4);
   const size_t parts = al((size_t)kVB * 8), pp = al((size_t)(nparts + 1) * 8);
   const size_t hist = al((size_t)(w->hist_cap + 2) * 8), st = al(sizeof(PcgState));
-  const size_t total = 7 * v64 + 3 * v32 + parts + 2 * pp + hist + st;
+  const size_t total = 7 * v64 + 6 * v32 + parts + 2 * pp + hist + st;
   ehyb_status_t s = device_alloc(&w->arena, total);
   if (s != EHYB_OK) {
     delete w;
@@ -262,7 +419,7 @@ ehyb_status_t work_get(ehyb_precond_t M, int hist_need, PcgWork** out) {
   char* b = (char*)w->arena;
   double** v[] = {&w->bp, &w->xp, &w->r, &w->p, &w->q, &w->z, &w->t};
   for (double** d : v) { *d = (double*)b; b += v64; }
-  float** f[] = {&w->r32, &w->t32, &w->z32};
+  float** f[] = {&w->r32, &w->t32, &w->z32, &w->p32, &w->q32, &w->d32};
   for (float** d : f) { *d = (float*)b; b += v32; }
   w->part = (double*)b; b += parts;
   w->pq_part = (double*)b; b += pp;
@@ -310,19 +467,36 @@ ehyb_status_t enqueue_chunk(ehyb_precond_t M, PcgWork* w, cudaStream_t s) {
   return EHYB_OK;
 }
 
-ehyb_status_t run_chunk(ehyb_precond_t M, PcgWork* w, cudaStream_t s) {
-  if (!w->graph) {
+// inner FP32 iterations: A's low-precision values, G's low-precision values, FP32 vectors
+ehyb_status_t enqueue_chunk32(ehyb_precond_t M, PcgWork* w, cudaStream_t s) {
+  const DevPlan& D = M->plan->dev;
+  const int64_t n = w->n;
+  for (int k = 0; k < kChunk; ++k) {
+    DotOut dot{w->pq_part, &w->st->arrive_pq, &w->st->pq};
+    CKP(launch_ehyb_lowp(D, M->plan->lowp, w->p32, w->q32, 0, s, &dot, &w->st->done));
+    pcg_update32<<<kVB, kVT, 0, s>>>(n, w->d32, w->p32, w->q32, w->r32, w->hist, w->st, w->part);
+    ehyb_status_t st = apply_precond(M, w, s, &w->st->done);
+    if (st != EHYB_OK) return st;
+    pcg_pupdate32<<<kVB, kVT, 0, s>>>(n, w->z32, w->p32, w->st);
+    CKP(cudaGetLastError());
+  }
+  return EHYB_OK;
+}
+
+ehyb_status_t run_chunk(ehyb_precond_t M, PcgWork* w, cudaStream_t s, bool inner32 = false) {
+  cudaGraphExec_t* g = inner32 ? &w->graph32 : &w->graph;
+  if (!*g) {
     cudaGraph_t graph;
     CKP(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
-    ehyb_status_t st = enqueue_chunk(M, w, w->cap);
+    ehyb_status_t st = inner32 ? enqueue_chunk32(M, w, w->cap) : enqueue_chunk(M, w, w->cap);
     cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
     if (st != EHYB_OK) return st;
     CKP(e);
-    e = cudaGraphInstantiate(&w->graph, graph, 0);
+    e = cudaGraphInstantiate(g, graph, 0);
     cudaGraphDestroy(graph);
     CKP(e);
   }
-  CKP(cudaGraphLaunch(w->graph, s));
+  CKP(cudaGraphLaunch(*g, s));
   return EHYB_OK;
 }
 
@@ -416,4 +590,97 @@ extern "C" ehyb_status_t ehyb_pcg_history(ehyb_precond_t M, double* rr, int32_t 
   if (k > 0) CKP(cudaMemcpy(rr, w->hist, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost));
   *n_out = k;
   return EHYB_OK;
+}
+
+extern "C" ehyb_status_t ehyb_pcg_refined(ehyb_plan_t P, ehyb_precond_t M, const double* b, double* x, double rtol,
+                                          int32_t max_iter, double inner_rtol, ehyb_cg_info_t* info, void* stream) {
+  if (!P || !M || !info) return EHYB_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  if (M->plan != P) return EHYB_ERR_INVALID_ARG;
+  if (P->host_only) return EHYB_ERR_UNSUPPORTED;
+  if (P->lowp == 0 || M->lowp == 0) return EHYB_ERR_UNSUPPORTED;  // needs A's and G's low-precision values
+  if (!(rtol >= 0.0) || max_iter < 0 || !(inner_rtol >= 0.0) || inner_rtol >= 1.0) return EHYB_ERR_INVALID_ARG;
+  const double delta = inner_rtol > 0.0 ? inner_rtol : 0.01;
+  const int64_t n = P->dev.n;
+  const double t0 = now_s();
+  if (n == 0) {
+    info->converged = 1;
+    return EHYB_OK;
+  }
+  if (!b || !x) return EHYB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  PcgWork* w = nullptr;
+  ehyb_status_t st = work_get(M, max_iter + 2, &w);
+  if (st != EHYB_OK) return st;
+  const DevPlan& D = P->dev;
+  CKP(launch_permute_f64(D, 1, b, w->bp, s));
+  CKP(launch_permute_f64(D, 1, x, w->xp, s));
+  pcg_norm2<<<kVB, kVT, 0, s>>>(n, w->bp, w->part);
+  double bb = 0.0;
+  if ((st = sum_part(w, s, &bb)) != EHYB_OK) return st;
+  const double bnorm = bb > 0.0 ? std::sqrt(bb) : 1.0;
+
+  // FP64 residual of x0; the first segment starts like a plain PCG on r / ||r||
+  CKP(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+  pcg_residual<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, nullptr, w->part);
+  double rr = 0.0;
+  if ((st = sum_part(w, s, &rr)) != EHYB_OK) return st;
+  int iters = 0, outer = 0, converged = std::sqrt(rr) <= rtol * bnorm ? 1 : 0;
+  double scale = std::sqrt(rr), best_rr = rr;
+  int stalls = 0;
+  if (!converged && rr > 0.0) {
+    pcg_inner_start<<<kVB, kVT, 0, s>>>(n, w->r, 1.0 / scale, w->r32, w->d32, w->part);
+    pcg_init_finish<<<1, 32, 0, s>>>(w->part, kVB, delta * delta, max_iter, w->hist, w->st);
+    CKP(cudaGetLastError());
+    if ((st = apply_precond(M, w, s, nullptr)) != EHYB_OK) return st;
+    copy_f32<<<kVB, kVT, 0, s>>>(n, w->z32, w->p32);
+    CKP(cudaGetLastError());
+    for (;;) {
+      PcgState h;
+      for (;;) {
+        CKP(cudaMemcpyAsync(&h, w->st, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CKP(cudaStreamSynchronize(s));
+        if (h.done) break;
+        if ((st = run_chunk(M, w, s, true)) != EHYB_OK) return st;
+      }
+      iters += h.it;
+      // replacement: x += s d, r = b - A x in FP64
+      pcg_correct<<<kVB, kVT, 0, s>>>(n, w->xp, w->d32, scale);
+      CKP(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+      pcg_residual<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, nullptr, w->part);
+      if ((st = sum_part(w, s, &rr)) != EHYB_OK) return st;
+      ++outer;
+      if (std::sqrt(rr) <= rtol * bnorm) {
+        converged = 1;
+        break;
+      }
+      if (h.breakdown || !(rr < 1e300) || iters >= max_iter) break;
+      if (rr < best_rr) {
+        best_rr = rr;
+        stalls = 0;
+      } else if (++stalls >= 3) {
+        break;  // three replacements without a better FP64 residual: FP32 has nothing left to give
+      }
+      const double ns = std::sqrt(rr);
+      const double ratio = scale / ns;
+      pcg_replace<<<kVB, kVT, 0, s>>>(n, w->r, 1.0 / ns, (float)ratio, w->r32, w->d32, w->p32, w->part);
+      pcg_replace_finish<<<1, 32, 0, s>>>(w->part, kVB, delta * delta, ratio * ratio, max_iter - iters, w->hist,
+                                          w->st);
+      CKP(cudaGetLastError());
+      scale = ns;
+      // finish the interrupted iteration on the replaced residual: z = M r, p = z + beta p
+      if ((st = apply_precond(M, w, s, nullptr)) != EHYB_OK) return st;
+      pcg_pupdate32_force<<<kVB, kVT, 0, s>>>(n, w->z32, w->p32, w->st);
+      CKP(cudaGetLastError());
+    }
+  }
+  CKP(launch_permute_f64(D, 0, w->xp, x, s));
+  CKP(cudaStreamSynchronize(s));
+  info->iterations = iters;
+  info->refinements = outer;
+  info->converged = converged;
+  info->relres = std::sqrt(rr) / bnorm;
+  info->relres_recursive = info->relres;
+  info->seconds = now_s() - t0;
+  return converged ? EHYB_OK : EHYB_ERR_NOT_CONVERGED;
 }

@@ -105,3 +105,34 @@ def test_pcg_errors(eh):
     assert e.value.status == 1
     st, info = P.pcg(M, b, torch.zeros_like(b), rtol=1e-14, max_iter=3)
     assert st == eh.EHYB_ERR_NOT_CONVERGED and info["iterations"] == 3
+
+
+@pytest.mark.parametrize("lowp_g", [1, 2])
+@pytest.mark.parametrize("which", ["tet", "hex"])
+def test_refined_pcg_reaches_1e10(eh, lowp_g, which):
+    # A's values in FP32 (BF16 values of A are too coarse for elasticity: u_bf16 * cond(A) > 1), G's values in
+    # FP32 or BF16
+    A = gen.tet_lap3d(N=20) if which == "tet" else gen.hex_elast3d(N=10, clamp_minz=True)
+    P = eh.Plan(A, lowp=1)
+    M = eh.Fsai(P, A, lowp=lowp_g)
+    xs = gen.uniform(A.n, 25)
+    b = oracle.spmv(A, xs)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, info = P.pcg_refined(M, bd, x, rtol=1e-10)
+    assert st == 0 and info["converged"] and info["refinements"] >= 2
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - oracle.spmv(A, xh)) <= 1.01e-10 * np.linalg.norm(b)   # the oracle's FP64 residual
+    x2 = torch.zeros_like(bd)
+    _, pinfo = P.pcg(M, bd, x2, rtol=1e-10)
+    assert info["iterations"] <= 1.5 * pinfo["iterations"] + 10, (info, pinfo)
+
+
+def test_refined_pcg_needs_low_precision_values(eh):
+    A = gen.tet_lap3d(N=6)
+    P = eh.Plan(A)                       # no FP32 copy of A
+    M = eh.Fsai(P, A, lowp=1)
+    b = torch.ones(A.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(eh.EhybError) as e:
+        P.pcg_refined(M, b, torch.zeros_like(b))
+    assert e.value.status == 7
