@@ -348,6 +348,12 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
   D.threads = opt.block_threads;
   D.er_layout = H.er_layout;
   D.max_part_rows = H.max_part_rows;
+  {  // batch depth: mean slab + sliced-ER slots per lane of a slice (measured: 6 is faster from about 32 up)
+    const double slots = (double)(H.slice_pos.empty() ? 0 : H.slice_pos.back()) +
+                         (double)(H.er_slice_pos.empty() ? 0 : H.er_slice_pos.back());
+    const double w = H.nslices ? slots / (32.0 * (double)H.nslices) : 0.0;
+    D.kbatch = (H.er_layout == 0 && w >= 32.0) ? 6 : 8;
+  }
   D.wait_timeout_ns = opt.wait_timeout_ns > 0 ? (uint64_t)opt.wait_timeout_ns : 1000000000ull;
   D.inject_wait_fault = opt.inject_wait_fault;
 

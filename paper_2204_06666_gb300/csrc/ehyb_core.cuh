@@ -110,26 +110,26 @@ __device__ __forceinline__ float load_val<uint16_t, float>(const uint16_t* p) {
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
-constexpr int kBatch = 8;   // slots whose loads are issued before their FMAs
+constexpr int kBatch = 8;   // slots whose loads are issued before their FMAs (default batch depth)
 constexpr int kStage = 16;  // elements of x per thread in flight while a slice of x is gathered
 
 // acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory.  Loads are issued
-// kBatch at a time ahead of their FMAs; the FMAs run in slot order.  (A predicated last batch measured
-// slower than this scalar remainder on both 3D workloads.)
-template <typename V, typename X>
+// KB at a time ahead of their FMAs; the FMAs run in slot order, so the result does not depend on KB.
+// (A predicated last batch measured slower than this scalar remainder on both 3D workloads.)
+template <typename V, typename X, int KB = kBatch>
 __device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
                                       const X* xs, X acc) {
   int k = 0;
-  for (; k + kBatch <= w; k += kBatch) {
-    X v[kBatch];
-    int c[kBatch];
+  for (; k + KB <= w; k += KB) {
+    X v[KB];
+    int c[KB];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < KB; ++u) {
       v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
       c[u] = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u)));
     }
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) acc = fma_t(v[u], xs[c[u]], acc);
+    for (int u = 0; u < KB; ++u) acc = fma_t(v[u], xs[c[u]], acc);
   }
   for (; k < w; ++k)
     acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k),
@@ -138,23 +138,23 @@ __device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* 
 }
 
 // acc += sum_{k<w} v[32k] * xg[c[32k]]: sliced extra-row slots of one lane, x from global memory
-template <typename V, typename X>
+template <typename V, typename X, int KB = kBatch>
 __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __restrict__ cp, int w,
                                     const X* __restrict__ xg, X acc) {
   int k = 0;
-  for (; k + kBatch <= w; k += kBatch) {
-    X v[kBatch];
-    int c[kBatch];
+  for (; k + KB <= w; k += KB) {
+    X v[KB];
+    int c[KB];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < KB; ++u) {
       v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
       c[u] = __ldcs(cp + 32 * (int64_t)(k + u));
     }
-    X xv[kBatch];
+    X xv[KB];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) xv[u] = __ldg(xg + c[u]);
+    for (int u = 0; u < KB; ++u) xv[u] = __ldg(xg + c[u]);
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) acc = fma_t(v[u], xv[u], acc);
+    for (int u = 0; u < KB; ++u) acc = fma_t(v[u], xv[u], acc);
   }
   for (; k < w; ++k) acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k), __ldg(xg + __ldcs(cp + 32 * (int64_t)k)), acc);
   return acc;
@@ -226,7 +226,8 @@ struct BlockState {
 // staged by one bulk asynchronous copy.
 // Returns false (uniformly across the block) when the staging wait ran
 // out of time.
-template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false, bool GATHER = false>
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false, bool GATHER = false,
+          int KB = kBatch>
 __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
                                                const V* __restrict__ er_val, const X* __restrict__ xp,
                                                X* __restrict__ y, const int p, X* xs, BlockState& bs) {
@@ -340,8 +341,9 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
         nwe = (int)((a.er_slice_pos[nxt + 1] - nepos) >> 5);
       }
     }
-    X acc = slab_dot<V, X>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
-    if (ER_SLICED) acc = er_dot<V, X>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc);
+    X acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
+    if (ER_SLICED)
+      acc = er_dot<V, X, KB>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc);
     for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
     if (sub == 0 && row < pe) {

@@ -4,6 +4,7 @@
 #include "ehyb_core.cuh"
 
 #include <cstdint>
+#include <type_traits>
 
 namespace ehyb {
 
@@ -11,7 +12,7 @@ namespace {
 
 using namespace core;
 
-template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false>
+template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false, int KB = kBatch>
 __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
                                                     const V* __restrict__ er_val, const X* __restrict__ xp,
                                                     X* __restrict__ y) {
@@ -29,8 +30,8 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     bs.bar_ready = 0;
     bs.phase = 0;
   }
-  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER>(a, ell_val, er_val, xp, y, blockIdx.x,
-                                                        reinterpret_cast<X*>(smem_raw), bs);
+  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB>(a, ell_val, er_val, xp, y, blockIdx.x,
+                                                            reinterpret_cast<X*>(smem_raw), bs);
 }
 
 template <typename X>
@@ -73,10 +74,20 @@ size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes) {
   return (b + 15) & ~(size_t)15;
 }
 
+// batch depth of the FP64 kernels for wide slices (see DevPlan::kbatch)
+constexpr int kWideBatch = 6;
+
 template <typename V, typename X>
 static cudaError_t set_smem(int bytes) {
   cudaError_t e;
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (std::is_same<V, double>::value) {
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true, kWideBatch>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, true, true, kWideBatch>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true, false, kWideBatch>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false, false, kWideBatch>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, false, kWideBatch>, attr, bytes))) return e;
+  }
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false>, attr, bytes))) return e;
@@ -109,6 +120,9 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false>
 static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArgs& a, const V* ev, const V* erv,
                        const X* xp, X* y) {
+  // FP64 kernels on plans with wide slices use the shallower batch (sliced-ER layout only)
+  constexpr bool kWideOk = std::is_same<V, double>::value && ER_SLICED;
+  const bool wide = kWideOk && P.kbatch == kWideBatch;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)P.nparts);
   cfg.blockDim = dim3((unsigned)P.threads);
@@ -119,7 +133,9 @@ static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArg
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
+  if (wide) cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kWideOk ? kWideBatch : kBatch>,
+                                a, ev, erv, xp, y);
+  else cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
 }
 
 template <typename V, typename X>
