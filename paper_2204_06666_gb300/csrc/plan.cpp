@@ -336,17 +336,42 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
     ga.swap(adj);
   }
 
-  // pseudo-peripheral start: the last vertex reached by a breadth-first search from vertex 0
+  // pseudo-peripheral start: the last vertex reached by a breadth-first search from vertex 0.  The graph
+  // is then renumbered in that search's order (neighbours get nearby numbers), so the second search and
+  // the growth below walk memory locally; `label` maps the new numbers back.
   std::vector<int32_t> order;
   int64_t comp0 = bfs_order(nv, gx, ga, 0, order);
-  int32_t start = order[(size_t)comp0 - 1];
+  std::vector<int32_t> label(order);  // new vertex -> old vertex
+  {
+    std::vector<int32_t> inv((size_t)nv);
+    for (int64_t k = 0; k < nv; ++k) inv[(size_t)label[(size_t)k]] = (int32_t)k;
+    std::vector<int64_t> rx((size_t)nv + 1, 0);
+    for (int64_t k = 0; k < nv; ++k) {
+      const int32_t o = label[(size_t)k];
+      rx[(size_t)k + 1] = rx[(size_t)k] + (gx[(size_t)o + 1] - gx[(size_t)o]);
+    }
+    std::vector<int32_t> ra((size_t)rx[(size_t)nv]);
+    parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
+      for (int64_t k = lo; k < hi; ++k) {
+        const int32_t o = label[(size_t)k];
+        int32_t* d = ra.data() + rx[(size_t)k];
+        int64_t m = 0;
+        for (int64_t e = gx[(size_t)o]; e < gx[(size_t)o + 1]; ++e) d[m++] = inv[(size_t)ga[(size_t)e]];
+        std::sort(d, d + m);
+      }
+    });
+    gx.swap(rx);
+    ga.swap(ra);
+  }
+  const int32_t start = (int32_t)(comp0 - 1);  // the search's last vertex of the first component
   bfs_order(nv, gx, ga, start, order);
 
   int64_t maxdeg = 0;
   for (int64_t v = 0; v < nv; ++v) maxdeg = std::max(maxdeg, gx[(size_t)v + 1] - gx[(size_t)v]);
   GainQueue q(nv, (int)maxdeg + 2);
   std::vector<int32_t> conn((size_t)nv, 0), touched, members, stamp((size_t)nv, -1);
-  std::vector<int64_t> next_row(first.begin(), first.end() - 1);  // first unassigned row of each vertex
+  std::vector<int64_t> next_row((size_t)nv);  // first unassigned row of each (new) vertex
+  for (int64_t v = 0; v < nv; ++v) next_row[(size_t)v] = first[(size_t)label[(size_t)v]];
   std::vector<char> done((size_t)nv, 0);
   int64_t cursor = 0, assigned = 0;
   auto next_free = [&]() -> int32_t {
@@ -360,7 +385,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
     int32_t size = 0;
     // take as many of v's remaining rows as the part holds
     auto add = [&](int32_t v) {
-      const int64_t left = first[(size_t)v + 1] - next_row[(size_t)v];
+      const int64_t left = first[(size_t)label[(size_t)v] + 1] - next_row[(size_t)v];
       const int64_t take = std::min<int64_t>(left, (int64_t)cap - size);
       for (int64_t k = 0; k < take; ++k) part[(size_t)next_row[(size_t)v]++] = p;
       size += (int32_t)take;
