@@ -84,6 +84,8 @@ typedef struct {
   int32_t tuner;             /* knob choice when slice_rows, ell_width_cap and ell_tpr are 0: 0 = Eq. 1 default,
                                 1 = learned model (ehyb_tuner_set_model) with the sweep as fallback when the plan
                                 runs over 2x the model's predicted time, 2 = exhaustive sweep (ehyb_tune_sweep) */
+  int32_t host_threads;      /* host threads of the planner's parallel phases (0 = the machine's, at most 32); the
+                                plan does not depend on it */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;

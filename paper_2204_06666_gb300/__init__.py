@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("smem_budget", ctypes.c_int32),
                 ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
                 ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32), ("tuner", ctypes.c_int32)]
+                ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32), ("tuner", ctypes.c_int32),
+                ("host_threads", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

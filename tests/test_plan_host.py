@@ -149,3 +149,20 @@ def test_sliced_extra_rows_padding_is_small_on_hex():
     A = gen.hex_elast3d(N=30)
     info = _plan(A, slice_rows=6770).info()
     assert info["er_stored"] <= 1.16 * info["er_nnz"]   # 1.150 here, 1.085 on the 70^3 benchmark matrix
+
+
+@pytest.mark.parametrize("which", ["hex", "tet", "random"])
+def test_plan_does_not_depend_on_host_threads(which):
+    # the planner's parallel phases (adjacency, supervariables, renumbering, encoding) must give the same plan
+    if which == "hex":
+        A = gen.hex_elast3d(N=12)
+    elif which == "tet":
+        A = gen.tet_lap3d(N=16, dirichlet=False)
+    else:
+        A = gen.random_csr(20000, 9, mean_row=9, empty_frac=0.02, long_rows=3, long_len=900, duplicates=True)
+    ref = _plan(A, slice_rows=900, host_threads=1).export()
+    for t in (2, 3, 8):
+        ex = _plan(A, slice_rows=900, host_threads=t).export()
+        for k in ("new_to_old", "part_ptr", "slice_ptr", "slice_pos", "ell_col", "ell_val", "er_slice_pos", "er_scol",
+                  "er_sval", "row_ell_count", "row_er_count"):
+            assert np.array_equal(np.asarray(ref[k]), np.asarray(ex[k])), (t, k)
