@@ -31,6 +31,7 @@ struct BatchPlan {
   const double* x;  // caller's x (original numbering)
   double* y;        // caller's y (original numbering)
   int64_t n;
+  int32_t kbatch;   // the plan's batch depth (6 on wide slices, else 8)
 };
 
 constexpr int kMaxThreads = 1024;  // block size: 512 when two or more blocks fit an SM, else 1024
@@ -53,9 +54,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batch_kernel(const BatchPlan* 
     if (t >= ntiles) break;
     const int2 tl = tiles[t];
     const BatchPlan& bp = plans[tl.x];
-    if (!partition_spmv<double, double, true, true, false, true>(bp.a, bp.ell_val, bp.er_val, bp.x, bp.y, tl.y,
-                                                                 reinterpret_cast<double*>(smem_raw), bs))
-      break;
+    double* xs = reinterpret_cast<double*>(smem_raw);
+    const bool ok =
+        bp.kbatch == 6
+            ? partition_spmv<double, double, true, true, false, true, 6>(bp.a, bp.ell_val, bp.er_val, bp.x, bp.y,
+                                                                         tl.y, xs, bs)
+            : partition_spmv<double, double, true, true, false, true>(bp.a, bp.ell_val, bp.er_val, bp.x, bp.y, tl.y,
+                                                                      xs, bs);
+    if (!ok) break;
   }
   __syncthreads();
   if (threadIdx.x == 0) {  // the last block out resets the queue for the next launch
@@ -127,6 +133,7 @@ extern "C" ehyb_status_t ehyb_batch_create(int32_t count, const ehyb_plan_t* pla
     bp.ell_val = P->dev.ell_val;
     bp.er_val = P->dev.er_sval;
     bp.n = P->dev.n;
+    bp.kbatch = P->dev.kbatch;
     b->table.push_back(bp);
     b->max_n = std::max(b->max_n, P->dev.n);
     b->smem = std::max(b->smem, ehyb_smem_bytes(P->dev, 8));

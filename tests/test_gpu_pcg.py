@@ -136,3 +136,40 @@ def test_refined_pcg_needs_low_precision_values(eh):
     with pytest.raises(eh.EhybError) as e:
         P.pcg_refined(M, b, torch.zeros_like(b))
     assert e.value.status == 7
+
+
+def test_pcg_from_a_nonzero_start_and_empty_matrix(eh):
+    A = gen.tet_lap3d(N=12)
+    P = eh.Plan(A, lowp=1)
+    M = eh.Fsai(P, A, lowp=1)
+    xs = gen.uniform(A.n, 31)
+    b = oracle.spmv(A, xs)
+    bd = torch.from_numpy(b).cuda()
+    x0 = torch.from_numpy(xs + 1e-3 * gen.uniform(A.n, 32)).cuda()      # close to the solution
+    for solve in (P.pcg, P.pcg_refined):
+        x = x0.clone()
+        st, info = solve(M, bd, x, rtol=1e-10)
+        assert st == 0 and info["converged"]
+        assert np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) <= 1.01e-10 * np.linalg.norm(b)
+    x = torch.zeros_like(bd)                                            # b = 0 and x0 = 0: converged at once
+    st, info = P.pcg(M, torch.zeros_like(bd), x, rtol=1e-10)
+    assert st == 0 and info["iterations"] == 0 and torch.count_nonzero(x) == 0
+    E = gen.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    PE = eh.Plan(E)
+    ME = eh.Fsai(PE, E)
+    z = torch.zeros(1, dtype=torch.float64, device="cuda")[:0]
+    st, info = PE.pcg(ME, z, z.clone())
+    assert st == 0 and info["converged"]
+
+
+def test_fsai_missing_diagonal_is_refused(eh):
+    A = gen.tet_lap3d(N=6)
+    S = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n)).tolil()
+    S[5, 5] = 0.0
+    S = S.tocsr()
+    S.eliminate_zeros()                                                 # row 5 loses its diagonal entry
+    B = gen.CSR(A.n, S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data.copy())
+    P = eh.Plan(B)
+    with pytest.raises(eh.EhybError) as e:
+        eh.Fsai(P, B)
+    assert e.value.status == 1

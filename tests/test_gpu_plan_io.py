@@ -53,3 +53,18 @@ def test_loaded_plan_low_precision_copies(eh, tmp_path):
     Q.spmv_lowp(x, y2)
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
+
+
+def test_loaded_plan_solves_like_the_saved_one(eh, tmp_path):
+    # CG on a loaded plan (FP64 and FP32 residual replacement) gives the iterations and bits of the original
+    A = gen.tet_lap3d(N=14)
+    P = eh.Plan(A, lowp=1)
+    f = str(tmp_path / "tet.ehyb")
+    P.save(f)
+    Q = eh.Plan.load(f, lowp=1)
+    b = torch.from_numpy(oracle.spmv(A, gen.uniform(A.n, 5))).cuda()
+    for refine in (0, 3):
+        x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+        _, i1 = P.cg(b, x1, rtol=1e-10, refine=refine)
+        _, i2 = Q.cg(b, x2, rtol=1e-10, refine=refine)
+        assert i1["iterations"] == i2["iterations"] and torch.equal(x1, x2)
