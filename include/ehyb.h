@@ -56,7 +56,9 @@ typedef enum {
   EHYB_ERR_NOT_CONVERGED = 8, /* iterative solver stopped at max_iter */
   EHYB_ERR_TIMEOUT = 9,       /* a bounded device-side wait ran out; results of that call are invalid */
   EHYB_ERR_NO_DEVICE = 10,    /* no CUDA device */
-  EHYB_ERR_IO = 11            /* a plan file cannot be written or read, or fails its checksum / structure checks */
+  EHYB_ERR_IO = 11,           /* a plan file cannot be written or read, or fails its checksum / structure checks */
+  EHYB_ERR_BOUNDS = 12        /* bounds-checked build only: a kernel computed an index outside its buffer (the access
+                                 was skipped); reported by ehyb_plan_check like EHYB_ERR_TIMEOUT */
 } ehyb_status_t;
 
 typedef enum { EHYB_F64 = 0, EHYB_F32 = 1, EHYB_BF16 = 2 } ehyb_dtype_t;
@@ -422,6 +424,10 @@ ehyb_status_t ehyb_mlp_adam(float* params, float* m, float* v, const float* grad
 /* Allow `count` more device allocations by this library, then fail them with EHYB_ERR_OOM;
  * a negative count switches the hook off.  Used to test the out-of-memory paths. */
 void ehyb_test_fail_allocs_after(int32_t count);
+/* Test hook: runs the kernels' index check on index i against limit lim in a one-thread kernel with its own
+ * status word and returns that word (EHYB_ERR_BOUNDS for an index outside [0, lim) in the bounds-checked
+ * build, always EHYB_OK in the default build); synchronous.  Nothing is read or written at i. */
+ehyb_status_t ehyb_test_bounds_probe(int64_t i, int64_t lim);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,8 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 STATUS = {0: "EHYB_OK", 1: "EHYB_ERR_INVALID_ARG", 2: "EHYB_ERR_NOT_SQUARE", 3: "EHYB_ERR_INDEX_RANGE",
           4: "EHYB_ERR_TOO_LARGE", 5: "EHYB_ERR_OOM", 6: "EHYB_ERR_CUDA", 7: "EHYB_ERR_UNSUPPORTED",
-          8: "EHYB_ERR_NOT_CONVERGED", 9: "EHYB_ERR_TIMEOUT", 10: "EHYB_ERR_NO_DEVICE", 11: "EHYB_ERR_IO"}
+          8: "EHYB_ERR_NOT_CONVERGED", 9: "EHYB_ERR_TIMEOUT", 10: "EHYB_ERR_NO_DEVICE", 11: "EHYB_ERR_IO",
+          12: "EHYB_ERR_BOUNDS"}
 EHYB_OK, EHYB_ERR_TIMEOUT, EHYB_ERR_NOT_CONVERGED, EHYB_ERR_IO = 0, 9, 8, 11
 
 
@@ -101,6 +102,7 @@ _sig("ehyb_status_string", [ctypes.c_int], ctypes.c_char_p)
 _sig("ehyb_last_cuda_error", [], ctypes.c_char_p)
 _sig("ehyb_options_default", [ctypes.POINTER(Options)], None)
 _sig("ehyb_test_fail_allocs_after", [_I32], None)
+_sig("ehyb_test_bounds_probe", [_I64, _I64])
 _sig("ehyb_plan_create_csr", [_I64, _I64, _I64, _P, _P, _P, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)])
 _sig("ehyb_destroy", [_P])
 _sig("ehyb_spmv", [_P, _P, _P, _P])
@@ -247,6 +249,10 @@ def ehyb_plan_load(path: str, opt: Options | None, stream, out: ctypes.c_void_p)
 
 def ehyb_test_fail_allocs_after(count: int):
     _lib.ehyb_test_fail_allocs_after(count)
+
+
+def ehyb_test_bounds_probe(i: int, lim: int) -> int:
+    return int(_lib.ehyb_test_bounds_probe(int(i), int(lim)))
 
 
 # ---------------------------------------------------------------- owning wrappers

@@ -1,4 +1,8 @@
-"""Compile libehyb.so in-tree for sm_103a (nvcc for .cu, g++ for host .cpp, parallel, no cmake)."""
+"""Compile libehyb.so in-tree for sm_103a (nvcc for .cu, g++ for host .cpp, parallel, no cmake).
+
+`build(checked=True)` (or `--checked`) compiles the bounds-checked variant libehyb_checked.so
+(-DEHYB_BOUNDS_CHECK=1: every index the kernels compute is tested against its buffer; select it at run
+time with EHYB_LIBRARY)."""
 from __future__ import annotations
 
 import glob
@@ -12,6 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libehyb.so")
+OUT_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libehyb_checked.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -24,27 +30,29 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "ehyb.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out_dir, lib = (OUT_CHECKED, LIB_CHECKED) if checked else (OUT, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", os.path.join(CUDA, "include")]
+    defs = ["-DEHYB_BOUNDS_CHECK=1"] if checked else []
     procs, objs = [], []
     for src in _sources():
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
             cmd = [os.path.join(CUDA, "bin", "nvcc"), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", src, "-o", obj]
+                   "-Xptxas", "-v" if verbose else "-O3", *defs, *inc, "-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-c", src, "-o", obj]
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *defs, *inc, "-c", src, "-o", obj]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     failed = []
     for src, p in procs:
@@ -60,9 +68,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     libdir = os.path.join(CUDA, "lib64")
     subprocess.run(["g++", "-shared", "-o", tmp, *objs, "-L", libdir, "-lcudart", "-Wl,-rpath," + libdir],
                    check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -165,6 +165,7 @@ const char* ehyb_status_string(ehyb_status_t s) {
     case EHYB_ERR_TIMEOUT: return "device wait timed out";
     case EHYB_ERR_NO_DEVICE: return "no CUDA device";
     case EHYB_ERR_IO: return "plan file unreadable, unwritable or invalid";
+    case EHYB_ERR_BOUNDS: return "device-side bounds check failed (checked build)";
   }
   return "unknown status";
 }

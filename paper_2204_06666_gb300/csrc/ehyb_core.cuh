@@ -31,6 +31,22 @@ namespace core {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTimeoutCode = 9;  // EHYB_ERR_TIMEOUT
+constexpr int kBoundsCode = 12;  // EHYB_ERR_BOUNDS
+
+// Checked build (-DEHYB_BOUNDS_CHECK=1): every index the kernels compute into shared memory, x and y is
+// tested against its buffer; a violation records EHYB_ERR_BOUNDS in the plan status word and the access
+// goes to index 0 instead.  The default build compiles the tests away.
+#ifndef EHYB_BOUNDS_CHECK
+#define EHYB_BOUNDS_CHECK 0
+#endif
+template <typename I>
+__device__ __forceinline__ I checked(I i, int64_t lim, int32_t* status) {
+  if (EHYB_BOUNDS_CHECK && ((int64_t)i < 0 || (int64_t)i >= lim)) {
+    atomicCAS(status, 0, kBoundsCode);
+    return I(0);
+  }
+  return i;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -118,7 +134,7 @@ constexpr int kStage = 16;  // elements of x per thread in flight while a slice 
 // (A predicated last batch measured slower than this scalar remainder on both 3D workloads.)
 template <typename V, typename X, int KB = kBatch>
 __device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
-                                      const X* xs, X acc) {
+                                      const X* xs, X acc, int lim, int32_t* status) {
   int k = 0;
   for (; k + KB <= w; k += KB) {
     X v[KB];
@@ -126,21 +142,22 @@ __device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* 
 #pragma unroll
     for (int u = 0; u < KB; ++u) {
       v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
-      c[u] = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u)));
+      c[u] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u))), lim, status);
     }
 #pragma unroll
     for (int u = 0; u < KB; ++u) acc = fma_t(v[u], xs[c[u]], acc);
   }
   for (; k < w; ++k)
     acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k),
-                xs[__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)k))], acc);
+                xs[checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)k)), lim, status)],
+                acc);
   return acc;
 }
 
 // acc += sum_{k<w} v[32k] * xg[c[32k]]: sliced extra-row slots of one lane, x from global memory
 template <typename V, typename X, int KB = kBatch>
 __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __restrict__ cp, int w,
-                                    const X* __restrict__ xg, X acc) {
+                                    const X* __restrict__ xg, X acc, int64_t lim, int32_t* status) {
   int k = 0;
   for (; k + KB <= w; k += KB) {
     X v[KB];
@@ -148,7 +165,7 @@ __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __r
 #pragma unroll
     for (int u = 0; u < KB; ++u) {
       v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
-      c[u] = __ldcs(cp + 32 * (int64_t)(k + u));
+      c[u] = checked(__ldcs(cp + 32 * (int64_t)(k + u)), lim, status);
     }
     X xv[KB];
 #pragma unroll
@@ -156,12 +173,16 @@ __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __r
 #pragma unroll
     for (int u = 0; u < KB; ++u) acc = fma_t(v[u], xv[u], acc);
   }
-  for (; k < w; ++k) acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k), __ldg(xg + __ldcs(cp + 32 * (int64_t)k)), acc);
+  for (; k < w; ++k)
+    acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k), __ldg(xg + checked(__ldcs(cp + 32 * (int64_t)k), lim, status)),
+                acc);
   return acc;
 }
 
 struct KArgs {
   int32_t tpr_log2, er_tpr_log2;
+  int64_t n;              // rows (= columns) of the matrix
+  int64_t smem_elems;     // capacity of the staged slice of x (elements); checked build only
   const int64_t* er_slice_pos;
   const int32_t* er_scol;
   const int32_t* er_scol_old;
@@ -267,18 +288,19 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     for (int i0 = pb + tid; i0 < pe; i0 += kStage * bd) {
       int c[kStage];
 #pragma unroll
-      for (int u = 0; u < kStage; ++u) c[u] = (i0 + u * bd < pe) ? __ldg(a.new_to_old + i0 + u * bd) : -1;
+      for (int u = 0; u < kStage; ++u)
+        c[u] = (i0 + u * bd < pe) ? checked(__ldg(a.new_to_old + i0 + u * bd), a.n, a.status) : -1;
       X v[kStage];
 #pragma unroll
       for (int u = 0; u < kStage; ++u) v[u] = c[u] >= 0 ? __ldg(xp + c[u]) : X(0);
 #pragma unroll
       for (int u = 0; u < kStage; ++u)
-        if (i0 + u * bd < pe) xs[i0 + u * bd - a0] = v[u];
+        if (i0 + u * bd < pe) xs[checked(i0 + u * bd - a0, a.smem_elems, a.status)] = v[u];
     }
   } else {
     // plain loads: everything when the source is unaligned, else the ragged tail [a1, pe)
     const int lo = bulk_bytes ? (a1 > pb ? a1 : pb) : pb;
-    for (int i = lo + tid; i < pe; i += blockDim.x) xs[i - a0] = xp[i];
+    for (int i = lo + tid; i < pe; i += blockDim.x) xs[checked(i - a0, a.smem_elems, a.status)] = xp[i];
   }
   if (tid == 0) {
     int ok = 1;
@@ -341,14 +363,15 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
         nwe = (int)((a.er_slice_pos[nxt + 1] - nepos) >> 5);
       }
     }
-    X acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0));
+    X acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0), pe - pb, a.status);
     if (ER_SLICED)
-      acc = er_dot<V, X, KB>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc);
+      acc = er_dot<V, X, KB>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc,
+                             a.n, a.status);
     for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
     if (sub == 0 && row < pe) {
-      if (SCATTER) y[a.new_to_old[row]] = acc;
-      else y[row] = acc;
+      if (SCATTER) y[checked(a.new_to_old[row], a.n, a.status)] = acc;
+      else y[checked(row, a.n, a.status)] = acc;
       if (dot) dacc = fma((double)acc, a.dot_self ? (double)acc : (double)xsl[row - pb], dacc);
     }
     i = inxt;
@@ -399,20 +422,21 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           v[u] = load_val<V, X>(er_val + k + u * etpr);
-          c[u] = __ldcs(a.er_col + k + u * etpr);
+          c[u] = checked(__ldcs(a.er_col + k + u * etpr), a.n, a.status);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) xv[u] = __ldg(xp + c[u]);
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc = fma_t(v[u], xv[u], acc);
       }
-      for (; k < k1; k += etpr) acc = fma_t(load_val<V, X>(er_val + k), __ldg(xp + __ldcs(a.er_col + k)), acc);
+      for (; k < k1; k += etpr)
+        acc = fma_t(load_val<V, X>(er_val + k), __ldg(xp + checked(__ldcs(a.er_col + k), a.n, a.status)), acc);
     }
     for (int off = etpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     if (esub == 0 && e < e1) {
       const int row = a.er_row[e];
-      if (SCATTER) y[a.new_to_old[row]] += acc;
-      else y[row] += acc;
+      if (SCATTER) y[checked(a.new_to_old[row], a.n, a.status)] += acc;
+      else y[checked(row, a.n, a.status)] += acc;
     }
   }
   return true;
@@ -428,6 +452,8 @@ inline int ilog2(int v) {
 inline KArgs make_kargs(const DevPlan& P) {
   KArgs a;
   a.tpr_log2 = ilog2(P.tpr);
+  a.n = P.n;
+  a.smem_elems = (int64_t)P.max_part_rows + 2;  // launches set the exact capacity of their shared memory
   a.er_tpr_log2 = ilog2(P.er_tpr);
   a.er_slice_pos = P.er_slice_pos;
   a.er_scol = P.er_scol;

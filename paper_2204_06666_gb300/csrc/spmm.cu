@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(512) spmm_kernel(KArgs a, const double* __rest
   }
   {
     const int64_t lo = bulk_bytes ? (a1 > e0 ? a1 : e0) : e0;
-    for (int64_t i = lo + tid; i < e1; i += blockDim.x) xs[i - a0] = xc[i];
+    for (int64_t i = lo + tid; i < e1; i += blockDim.x) xs[checked(i - a0, a.smem_elems, a.status)] = xc[i];
   }
   if (tid == 0) {
     int ok = 1;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(512) spmm_kernel(KArgs a, const double* __rest
     const uint16_t* cp = a.ell_col + pos + lane;
     for (int kk = 0; kk < w; ++kk) {
       const double v = __ldcs(vp + 32 * (int64_t)kk);
-      const int c = __ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)kk));
+      const int c = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)kk)), pe - pb, a.status);
       const double* xr = xsl + c * KC;
 #pragma unroll
       for (int j = 0; j < KC; ++j) acc[j] = fma(v, xr[j], acc[j]);
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(512) spmm_kernel(KArgs a, const double* __rest
     const int32_t* ecp = a.er_scol + epos + lane;
     for (int kk = 0; kk < we; ++kk) {
       const double v = __ldcs(evp + 32 * (int64_t)kk);
-      const double* xr = xc + (int64_t)__ldcs(ecp + 32 * (int64_t)kk) * KC;
+      const double* xr = xc + (int64_t)checked(__ldcs(ecp + 32 * (int64_t)kk), a.n, a.status) * KC;
 #pragma unroll
       for (int j = 0; j < KC; ++j) acc[j] = fma(v, __ldg(xr + j), acc[j]);
     }
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(512) spmm_kernel(KArgs a, const double* __rest
       for (int off = tpr >> 1; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(FULL, acc[j], off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
     if (sub == 0 && row < pe) {
-      double* yr = Y + (int64_t)a.new_to_old[row] * k + c0;
+      double* yr = Y + (int64_t)checked(a.new_to_old[row], a.n, a.status) * k + c0;
 #pragma unroll
       for (int j = 0; j < KC; ++j) yr[j] = acc[j];
     }
@@ -132,7 +132,9 @@ cudaError_t launch_chunk(const DevPlan& D, const double* xc, double* Y, int k, i
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  spmm_kernel<KC><<<D.nparts, 512, smem, s>>>(make_kargs(D), D.ell_val, D.er_sval, xc, Y, k, c0);
+  KArgs a = make_kargs(D);
+  a.smem_elems = (int64_t)(smem / sizeof(double));
+  spmm_kernel<KC><<<D.nparts, 512, smem, s>>>(a, D.ell_val, D.er_sval, xc, Y, k, c0);
   return cudaGetLastError();
 }
 

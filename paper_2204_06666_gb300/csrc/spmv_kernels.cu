@@ -2,6 +2,7 @@
 // the gather / scatter permutations and the plain vector-CSR baseline.  The fused kernel body lives
 // in ehyb_core.cuh.
 #include "ehyb_core.cuh"
+#include "../../include/ehyb.h"
 
 #include <cstdint>
 #include <type_traits>
@@ -59,6 +60,8 @@ __global__ void csr_kernel(int64_t n, int tpr_log2, const int64_t* __restrict__ 
   for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
   if (sub == 0 && row < n) y[row] = acc;
 }
+
+__global__ void bounds_probe_kernel(int64_t i, int64_t lim, int32_t* status) { (void)checked(i, lim, status); }
 
 int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
@@ -142,6 +145,7 @@ template <typename V, typename X>
 static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const V* erv_sl, const X* xp, X* y,
                          int scatter, size_t smem, cudaStream_t s, const DotOut* dot, const int32_t* skip) {
   KArgs a = make_kargs(P);
+  a.smem_elems = (int64_t)(smem / sizeof(X));
   if (dot) {
     a.dot_part = dot->part;
     a.dot_arrive = dot->arrive;
@@ -197,3 +201,17 @@ cudaError_t launch_csr_f64(int64_t n, const int64_t* rp, const int32_t* col, con
 }
 
 }  // namespace ehyb
+
+extern "C" ehyb_status_t ehyb_test_bounds_probe(int64_t i, int64_t lim) {
+  int32_t* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int32_t)) != cudaSuccess) return EHYB_ERR_CUDA;
+  int32_t h = 0;
+  cudaError_t e = cudaMemset(d, 0, sizeof(int32_t));
+  if (e == cudaSuccess) {
+    ehyb::bounds_probe_kernel<<<1, 1>>>(i, lim, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? (ehyb_status_t)h : EHYB_ERR_CUDA;
+}
