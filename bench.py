@@ -120,11 +120,13 @@ class ClockSampler:
                 if rows else None}
 
 
-def cpu_baseline(A, x, budget_s: float = 10.0):
-    """The oracle CSR SpMV (plain C, one thread) on a bounded sample: whole row blocks until budget."""
+def cpu_baseline(A, x, budget_s: float = 10.0, y_gpu=None):
+    """The oracle CSR SpMV (plain C, one thread) on a bounded sample: whole row blocks until budget.  With the
+    GPU result y_gpu, also the relative L2 error of y_gpu on the rows the oracle computed."""
     import oracle
     n = A.n
     y = np.zeros(n)
+    done = np.zeros(n, bool)
     block = max(1, n // 16)
     t0 = time.perf_counter()
     rows = flops = 0
@@ -132,12 +134,19 @@ def cpu_baseline(A, x, budget_s: float = 10.0):
     while time.perf_counter() - t0 < budget_s:
         r1 = min(n, r + block)
         oracle.spmv_rows(A, x, r, r1, y)
+        done[r:r1] = True
         flops += 2 * int(A.row_ptr[r1] - A.row_ptr[r])
         rows += r1 - r
         r = 0 if r1 >= n else r1
     dt = time.perf_counter() - t0
-    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rows} rows in blocks of {block} of the same matrix (plain C CSR, 1 thread, {dt:.1f} s)"}
+    out = {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+           "sample": f"{rows} rows in blocks of {block} of the same matrix (plain C CSR, 1 thread, {dt:.1f} s)"}
+    if y_gpu is not None:
+        ref = y[done]
+        out["parity"] = {"rows_checked": int(done.sum()),
+                         "rel_l2": float(np.linalg.norm(y_gpu[done] - ref) / max(np.linalg.norm(ref), 1e-300)),
+                         "tolerance": 1e-13}
+    return out
 
 
 def kernel_source_sha() -> str:
@@ -401,7 +410,9 @@ def run_ehyb(args):
                               "x_spmv": plan_ms / ms_per_step, "plan_file": plan_io},
             "e2e": e2e, "gpu_launches": (1 if fused else 2) * args.steps, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(A, x, args.cpu_seconds)
+        plan.spmv(xd, yd)
+        torch.cuda.synchronize()
+        line["cpu_baseline"] = cpu_baseline(A, x, args.cpu_seconds, yd.cpu().numpy())
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
