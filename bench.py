@@ -149,12 +149,15 @@ def cpu_baseline(A, x, budget_s: float = 10.0, y_gpu=None):
     return out
 
 
+KERNEL_SOURCES = ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu",
+                  "paper_2204_06666_gb300/csrc/plan.cpp", "paper_2204_06666_gb300/csrc/partition_ml.cpp")
+
+
 def kernel_source_sha() -> str:
     """Hash of the sources that decide the fused kernel's memory traffic (kernel body, launch, layout)."""
     import hashlib
     h = hashlib.sha256()
-    for rel in ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu",
-                "paper_2204_06666_gb300/csrc/plan.cpp"):
+    for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -247,7 +250,7 @@ def run_ehyb(args):
     x = gen.uniform(A.n, w["seed_x"])
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    plan = eh.Plan(A)
+    plan = eh.Plan(A, partitioner=args.partitioner)
     plan_ms = (time.perf_counter() - t0) * 1e3
     info = plan.info()
     xd = torch.from_numpy(x).to(dev)
@@ -311,7 +314,7 @@ def run_ehyb(args):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": None, "peak_source": f"{peak_src} copy bandwidth",
                 "alu": {"achieved": fp64_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak}}
-    traffic, tnote = recorded_traffic(args.workload)
+    traffic, tnote = recorded_traffic(args.workload + ("_multilevel" if args.partitioner else ""))
     roof["traffic"] = traffic
     if traffic is not None:
         roof["traffic_over_algorithmic"] = traffic / bytes_alg
@@ -400,6 +403,7 @@ def run_ehyb(args):
                        "l2": (f"inputs larger than L2 ({bytes_alg / 1e9:.2f} GB streamed from HBM every step)"
                               if bytes_alg > l2_bytes else
                               f"L2-resident ({bytes_alg / 1e6:.1f} MB), warm back-to-back steps, not flushed"),
+                       "partitioner": ["greedy growing", "multilevel"][args.partitioner],
                        "nparts": info["nparts"], "slice_rows": info["slice_rows"],
                        "er_fraction": info["er_nnz"] / A.nnz, "er_tpr": info["er_tpr"],
                        "block_threads": info["block_threads"]},
@@ -644,6 +648,8 @@ def main():
     ap.add_argument("--impl", default="ehyb", choices=["ehyb", "reference"])
     ap.add_argument("--workload", default="hex_elast3d_70", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-csr", action="store_true")
+    ap.add_argument("--partitioner", type=int, default=0, choices=[0, 1],
+                    help="PartVec of the SpMV plan: 0 greedy graph growing, 1 multilevel")
     ap.add_argument("--plan-io", action="store_true", help="also time saving the plan to a file and loading it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -78,7 +78,8 @@ typedef struct {
   int64_t wait_timeout_ns;   /* bound on each device-side wait; 0 = 1e9 (one second) */
   int32_t inject_wait_fault; /* test hook: the staging wait waits for a copy that is never issued */
   int32_t keep_host;         /* keep host copies of the plan arrays (ehyb_plan_export without device reads) */
-  uint64_t seed;             /* reserved for randomised partitioners; the in-house one is deterministic */
+  uint64_t seed;             /* seed of the multilevel partitioner's matching order (partitioner 1); the plan is a
+                                deterministic function of the matrix, the options and this seed */
   int32_t er_layout;         /* extra rows: 0 = sliced with the slab's own slices (one pass per slice, default),
                                 1 = CSR lines, er_tpr lanes each with a shuffle reduction, after a block barrier */
   int32_t part_nnz;          /* when slice_rows is 0: size partitions for about this many entries each (capped by
@@ -88,6 +89,10 @@ typedef struct {
                                 runs over 2x the model's predicted time, 2 = exhaustive sweep (ehyb_tune_sweep) */
   int32_t host_threads;      /* host threads of the planner's parallel phases (0 = the machine's, at most 32); the
                                 plan does not depend on it */
+  int32_t partitioner;       /* PartVec when part_vec is NULL (Sec. 3.1): 0 = greedy graph growing (default),
+                                1 = multilevel recursive bisection (heavy-edge coarsening, greedy-growing initial
+                                bisection, Fiduccia-Mattheyses refinement; ceil(n / slice_rows) parts of equal
+                                size); other values give EHYB_ERR_INVALID_ARG */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;

@@ -198,7 +198,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     return EHYB_ERR_INVALID_ARG;
   if (opt.er_layout < 0 || opt.er_layout > 1) return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
-      opt.part_nnz < 0 || opt.host_threads < 0 ||
+      opt.part_nnz < 0 || opt.host_threads < 0 || opt.partitioner < 0 || opt.partitioner > 1 ||
       opt.num_sms < 0 || opt.wait_timeout_ns < 0)
     return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows > 65536) return EHYB_ERR_TOO_LARGE;
@@ -271,6 +271,8 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   prm.er_layout = opt.er_layout;
   prm.part_vec = opt.part_vec;
   prm.threads = opt.host_threads;
+  prm.partitioner = opt.partitioner;
+  prm.seed = opt.seed;
   HostPlan& H = P->host;
   try {
     int rc = build_plan(prm, row_ptr, col, val, H);

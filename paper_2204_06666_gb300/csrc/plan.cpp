@@ -74,14 +74,6 @@ void make_lowp_copies(HostPlan& P, int lowp) {
 
 // ---------------------------------------------------------------- graph
 
-// splitmix64 finaliser: a well-mixed 64-bit hash of x
-static inline uint64_t mix64(uint64_t x) {
-  x += 0x9e3779b97f4a7c15ull;
-  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
-  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
-  return x ^ (x >> 31);
-}
-
 int planner_threads(int requested) {
   if (requested > 0) return requested;
   const unsigned hw = std::thread::hardware_concurrency();
@@ -91,7 +83,7 @@ int planner_threads(int requested) {
 // Graph of A for the partitioner: pattern of A + A^T without the diagonal, each list sorted and
 // duplicate-free.  The rows' own sorted lists are built in parallel; when the pattern is symmetric
 // (every FEM matrix) they already are the answer, otherwise the transpose is merged in.
-static void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& xadj,
+void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& xadj,
                           std::vector<int32_t>& adj) {
   std::vector<int64_t> len((size_t)n + 1, 0);
   std::unique_ptr<int32_t[]> tmp(new int32_t[(size_t)(n > 0 ? rp[n] : 0) + 1]);  // every used slot is written
@@ -175,7 +167,7 @@ static void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int 
 // neighbours) coincide -- the dofs of one node of a vector-valued FEM matrix, which are numbered
 // together.  sv_of[i] numbers the runs in row order; run v is rows first[v] .. first[v+1]-1.  Returns
 // the count (n when no two consecutive rows match).
-static int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int threads,
+int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int threads,
                               std::vector<int32_t>& sv_of, std::vector<int64_t>& first) {
   std::vector<uint64_t> key((size_t)n);
   parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
@@ -217,8 +209,47 @@ static int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const
   return nsv;
 }
 
+// The graph the partitioners cut: one vertex per supervariable (its weight is first[v+1] - first[v]
+// rows), an edge wherever two supervariables' rows are adjacent in the pattern of A + A^T; lists sorted.
+// Returns the vertex count.
+int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& first,
+                            std::vector<int64_t>& gx, std::vector<int32_t>& ga) {
+  std::vector<int64_t> xadj;
+  std::vector<int32_t> adj;
+  sym_adjacency(n, rp, col, threads, xadj, adj);
+  std::vector<int32_t> sv_of;
+  const int64_t nv = supervariables(n, xadj, adj, threads, sv_of, first);
+  if (nv < n) {
+    std::vector<int64_t> glen((size_t)nv + 1, 0);
+    std::vector<std::vector<int32_t>> lists((size_t)nv);
+    parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
+      for (int64_t v = lo; v < hi; ++v) {
+        const int64_t r = first[(size_t)v];  // the rows of a supervariable share their closed neighbourhood
+        std::vector<int32_t>& l = lists[(size_t)v];
+        for (int64_t e = xadj[(size_t)r]; e < xadj[(size_t)r + 1]; ++e) {
+          const int32_t u = sv_of[(size_t)adj[(size_t)e]];
+          if (u != v) l.push_back(u);
+        }
+        std::sort(l.begin(), l.end());
+        l.erase(std::unique(l.begin(), l.end()), l.end());
+        glen[(size_t)v + 1] = (int64_t)l.size();
+      }
+    });
+    gx.assign((size_t)nv + 1, 0);
+    for (int64_t v = 0; v < nv; ++v) gx[(size_t)v + 1] = gx[(size_t)v] + glen[(size_t)v + 1];
+    ga.resize((size_t)gx[(size_t)nv]);
+    for (int64_t v = 0; v < nv; ++v) std::copy(lists[(size_t)v].begin(), lists[(size_t)v].end(), ga.begin() + gx[(size_t)v]);
+    std::vector<int64_t>().swap(xadj);
+    std::vector<int32_t>().swap(adj);
+  } else {
+    gx.swap(xadj);
+    ga.swap(adj);
+  }
+  return nv;
+}
+
 // breadth-first order over every component; the first component starts at `s`
-static int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int32_t s,
+int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int32_t s,
                          std::vector<int32_t>& order) {
   std::vector<char> seen((size_t)n, 0);
   order.clear();
@@ -298,43 +329,10 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
   if (n == 0) return 0;
   if (cap < 1) cap = 1;
   threads = planner_threads(threads);
-  std::vector<int64_t> xadj;
-  std::vector<int32_t> adj;
-  sym_adjacency(n, rp, col, threads, xadj, adj);
-
-  // grow on the supervariable graph: vertex weight = rows of the supervariable; an edge wherever two
-  // supervariables' rows are adjacent
-  std::vector<int32_t> sv_of;
-  std::vector<int64_t> first;
-  const int64_t nv = supervariables(n, xadj, adj, threads, sv_of, first);
-  std::vector<int64_t> gx;
+  // grow on the supervariable graph: vertex weight = rows of the supervariable
+  std::vector<int64_t> first, gx;
   std::vector<int32_t> ga;
-  if (nv < n) {
-    std::vector<int64_t> glen((size_t)nv + 1, 0);
-    std::vector<std::vector<int32_t>> lists((size_t)nv);
-    parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
-      for (int64_t v = lo; v < hi; ++v) {
-        const int64_t r = first[(size_t)v];  // the rows of a supervariable share their closed neighbourhood
-        std::vector<int32_t>& l = lists[(size_t)v];
-        for (int64_t e = xadj[(size_t)r]; e < xadj[(size_t)r + 1]; ++e) {
-          const int32_t u = sv_of[(size_t)adj[(size_t)e]];
-          if (u != v) l.push_back(u);
-        }
-        std::sort(l.begin(), l.end());
-        l.erase(std::unique(l.begin(), l.end()), l.end());
-        glen[(size_t)v + 1] = (int64_t)l.size();
-      }
-    });
-    gx.assign((size_t)nv + 1, 0);
-    for (int64_t v = 0; v < nv; ++v) gx[(size_t)v + 1] = gx[(size_t)v] + glen[(size_t)v + 1];
-    ga.resize((size_t)gx[(size_t)nv]);
-    for (int64_t v = 0; v < nv; ++v) std::copy(lists[(size_t)v].begin(), lists[(size_t)v].end(), ga.begin() + gx[(size_t)v]);
-    std::vector<int64_t>().swap(xadj);
-    std::vector<int32_t>().swap(adj);
-  } else {
-    gx.swap(xadj);
-    ga.swap(adj);
-  }
+  const int64_t nv = supervariable_graph(n, rp, col, threads, first, gx, ga);
 
   // pseudo-peripheral start: the last vertex reached by a breadth-first search from vertex 0.  The graph
   // is then renumbered in that search's order (neighbours get nearby numbers), so the second search and
@@ -451,7 +449,8 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     part.assign(prm.part_vec, prm.part_vec + n);
     for (int64_t i = 0; i < n; ++i) nparts = std::max(nparts, part[(size_t)i] + 1);
   } else {
-    nparts = partition_graph(n, rp, col, prm.slice_rows, part, prm.threads);
+    nparts = prm.partitioner == 1 ? partition_multilevel(n, rp, col, prm.slice_rows, prm.seed, part, prm.threads)
+                                  : partition_graph(n, rp, col, prm.slice_rows, part, prm.threads);
   }
   P.nparts = nparts;
   const double t1 = now_ms();

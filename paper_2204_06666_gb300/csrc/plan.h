@@ -17,6 +17,8 @@ struct PlanParams {
   int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR
   const int32_t* part_vec = nullptr;
   int32_t threads = 0;        // host threads for the parallel phases (0 = the machine's); results do not depend on it
+  int32_t partitioner = 0;    // 0 greedy graph growing, 1 multilevel recursive bisection
+  uint64_t seed = 0;          // matching-order seed of the multilevel partitioner
 };
 
 struct HostPlan {
@@ -70,8 +72,40 @@ int32_t eq1_slice_rows(int64_t n, int tau, int P, int64_t budget_bytes);
 int32_t partition_graph(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t cap,
                         std::vector<int32_t>& part, int threads = 0);
 
+// Partition the same graph by multilevel recursive bisection into ceil(n / cap) parts of at most `cap`
+// vertices each; `seed` fixes the matching order of the coarsening.  Returns the number of parts; the
+// result does not depend on `threads`.
+int32_t partition_multilevel(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t cap, uint64_t seed,
+                             std::vector<int32_t>& part, int threads = 0);
+
 // host threads the planner uses for `requested` (0 = the machine's, at most 32)
 int planner_threads(int requested);
+
+// splitmix64 finaliser: a well-mixed 64-bit hash of x
+inline uint64_t mix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// pattern of A + A^T without the diagonal, each list sorted and duplicate-free
+void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& xadj,
+                   std::vector<int32_t>& adj);
+
+// supervariables of the graph (xadj, adj): maximal runs of consecutive rows with equal closed
+// neighbourhoods; run v is rows first[v] .. first[v+1]-1, sv_of maps a row to its run
+int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int threads,
+                       std::vector<int32_t>& sv_of, std::vector<int64_t>& first);
+
+// breadth-first order of every component of (xadj, adj), the first component from `s`; returns the size
+// of the first component
+int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int32_t s,
+                  std::vector<int32_t>& order);
+
+// the supervariable graph: vertex v = run v of `first`, an edge wherever two runs' rows are adjacent
+int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& first,
+                            std::vector<int64_t>& gx, std::vector<int32_t>& ga);
 
 // f(lo, hi) on `threads` contiguous pieces of [0, count), in parallel (in the caller when threads <= 1)
 template <typename F>

@@ -52,8 +52,7 @@ def test_traffic_record_tied_to_kernel_sources(tmp_path, monkeypatch):
     (prof / "ehyb_kernel_dram.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     # the hash is computed over ROOT's sources: copy them so the record matches
-    for rel in ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu",
-                "paper_2204_06666_gb300/csrc/plan.cpp"):
+    for rel in bench.KERNEL_SOURCES:
         dst = tmp_path / rel
         dst.parent.mkdir(parents=True, exist_ok=True)
         dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())

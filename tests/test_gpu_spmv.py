@@ -98,6 +98,34 @@ def test_tet126_full_size(eh):
     _check_fp(A, x, y)
 
 
+@pytest.mark.parametrize("name", ["hex", "tet", "powerlaw", "ragged_int"])
+def test_multilevel_partition_parity(eh, name):
+    # plans whose PartVec comes from the multilevel partitioner (equal parts, supervariables split across parts)
+    if name == "ragged_int":
+        A = gen.random_csr(3001, 4, mean_row=11, int_values=True, empty_frac=0.05, long_rows=5, long_len=1500,
+                           duplicates=True)
+        x = gen.int_vector(A.n, 104)
+        _, y = _run(eh, A, x, partitioner=1, slice_rows=37, block_threads=64)
+        assert np.array_equal(y, oracle.spmv(A, x))
+        return
+    A = {"hex": lambda: gen.hex_elast3d(N=16), "tet": lambda: gen.tet_lap3d(N=20),
+         "powerlaw": lambda: gen.tuner_matrix(1)}[name]()
+    x = gen.uniform(A.n, 13)
+    P, y = _run(eh, A, x, partitioner=1)
+    _check_fp(A, x, y)
+    G = eh.Plan(A)
+    assert P.info()["er_nnz"] < G.info()["er_nnz"]
+
+
+def test_multilevel_hex70_full_size(eh):
+    A = gen.hex_elast3d()
+    x = gen.uniform(A.n, 13)
+    P, y = _run(eh, A, x, partitioner=1)
+    _check_fp(A, x, y)
+    info = P.info()
+    assert info["nparts"] == 152 and info["er_nnz"] < 0.135 * A.nnz
+
+
 def test_permuted_entry_and_permute(eh):
     A = gen.hex_elast3d(N=10)
     x = gen.uniform(A.n, 5)
