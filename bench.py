@@ -425,6 +425,74 @@ def run_ehyb(args):
     return 0
 
 
+def run_transient(args):
+    """Many right-hand sides over time steps: implicit Euler for the heat equation on the Dirichlet tet
+    Laplacian, (K + c I) u_{t+1} = c u_t (lumped mass, c = 0.1 x the mean diagonal of K, about ten times
+    the explicit step), from u_0 ~ U[-1, 1) (seeded).  The plan and the preconditioner are built once; every
+    step forms b = (c I) u_t with the library's SpMV on a diagonal plan and solves to a 1e-10 relative
+    residual from u_t (warm start).  Per method: setup seconds, seconds and iterations per step, and how
+    many steps one setup costs.  The line's value is steps per second of the fastest method.
+    """
+    import torch
+    import gen
+    import paper_2204_06666_gb300 as eh
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    w = WORKLOADS[args.workload]
+    K = make_matrix(w)
+    rows = np.repeat(np.arange(K.n), np.diff(K.row_ptr))
+    c = 0.1 * float(K.val[K.col.astype(np.int64) == rows].mean())
+    S = gen.shifted(K, c)
+    u0 = torch.from_numpy(gen.uniform(K.n, w["seed_x"])).cuda()
+    t0 = time.perf_counter()
+    PS = eh.Plan(S, lowp=1)
+    plan_s = time.perf_counter() - t0
+    PR = eh.Plan(gen.scaled_identity(K.n, c))
+    out, finals = {}, {}
+    for name in ("fp64_cg", "fsai_pcg", "fsai_pcg_bf16_refined_0.01"):
+        t0 = time.perf_counter()
+        M = None if name == "fp64_cg" else eh.Fsai(PS, S, lowp=0 if name == "fsai_pcg" else 2)
+        setup_s = plan_s + time.perf_counter() - t0
+        u, b = u0.clone(), torch.empty_like(u0)
+        secs, iters = [], []
+        for step in range(args.transient_steps + 1):   # step 0 is untimed (first-use allocations)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            PR.spmv(u, b)
+            if name == "fp64_cg":
+                st, info = PS.cg(b, u, rtol=1e-10, max_iter=args.solver_max_iter)
+            elif name == "fsai_pcg":
+                st, info = PS.pcg(M, b, u, rtol=1e-10, max_iter=args.solver_max_iter)
+            else:
+                st, info = PS.pcg_refined(M, b, u, rtol=1e-10, max_iter=args.solver_max_iter, inner_rtol=0.01)
+            torch.cuda.synchronize()
+            if st != 0:
+                raise RuntimeError(f"{name} step {step}: {eh.STATUS.get(st, st)}")
+            if step > 0:
+                secs.append(time.perf_counter() - t1)
+                iters.append(info["iterations"])
+        step_s = statistics.median(secs)
+        finals[name] = u.cpu().numpy()
+        out[name] = {"setup_s": setup_s, "step_s": step_s, "steps_per_s": 1.0 / step_s,
+                     "iterations_per_step": float(np.mean(iters)), "iterations_first": iters[0],
+                     "setup_in_steps": setup_s / step_s,
+                     "total_s": setup_s + sum(secs)}
+        if M is not None:
+            M.close()
+    ref = finals["fp64_cg"]
+    for k in out:
+        out[k]["rel_diff_vs_fp64_cg"] = float(np.linalg.norm(finals[k] - ref) / np.linalg.norm(ref))
+    best = min(out, key=lambda k: out[k]["step_s"])
+    line = {"metric": "implicit time steps per second (heat equation, PCG to 1e-10 per step, warm start)",
+            "unit": "steps/s", "value": out[best]["steps_per_s"], "method": best, "higher_is_better": True,
+            "n_gpus": 1, "dtype": "f64+f32+bf16", "data": "synthetic",
+            "config": {"workload": args.workload, "n": K.n, "nnz": K.nnz, "desc": w["desc"], "shift_c": c,
+                       "steps": args.transient_steps},
+            "methods": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_solver(args):
     """Time to a 1e-10 relative residual: FP64 CG vs FP64 refinement around FP32 / BF16 inner CG, both as
     restarted refinement (refine 1 / 2) and as residual replacement that keeps the direction (refine 3 / 4),
@@ -662,6 +730,9 @@ def main():
     ap.add_argument("--spmm", action="store_true", help="time SpMM with --spmm-k right-hand sides")
     ap.add_argument("--spmm-k", type=int, nargs="+", default=[8, 32])
     ap.add_argument("--solver-reps", type=int, default=3)
+    ap.add_argument("--transient", action="store_true",
+                    help="time implicit-Euler steps (one plan and preconditioner, a PCG solve per step)")
+    ap.add_argument("--transient-steps", type=int, default=20)
     ap.add_argument("--solver-max-iter", type=int, default=50000)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -670,6 +741,8 @@ def main():
         return run_reference(args)
     if args.solver:
         return run_solver(args)
+    if args.transient:
+        return run_transient(args)
     if args.batch:
         return run_batch(args)
     if args.spmm:

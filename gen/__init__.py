@@ -139,6 +139,23 @@ def tet_lap3d(N: int = 126, jitter: float = 0.2, seed_mesh: int = 21, seed_perm:
     return CSR(n, rp, c, v, f"tet_lap3d_N{N}" + ("_dirichlet" if dirichlet else ""))
 
 
+def shifted(A: CSR, c: float) -> CSR:
+    """A + c I for a matrix whose every row stores its diagonal entry (the implicit-Euler operator
+    M/dt + K with a lumped mass M = (c dt) I); the pattern is unchanged."""
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.row_ptr))
+    diag = A.col.astype(np.int64) == rows
+    if np.count_nonzero(diag) != A.n or np.any(np.bincount(rows[diag], minlength=A.n) != 1):
+        raise ValueError("every row needs exactly one stored diagonal entry")
+    val = A.val.copy()
+    val[diag] += c
+    return CSR(A.n, A.row_ptr.copy(), A.col.copy(), val, A.name + f"_shift{c:g}")
+
+
+def scaled_identity(n: int, c: float) -> CSR:
+    """c I as a CSR matrix (one entry per row)."""
+    return CSR(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.full(n, float(c)), f"I_{c:g}")
+
+
 def coords(kind: str, N: int, jitter: float, seed_mesh: int, seed_perm: int) -> np.ndarray:
     """Jittered node coordinates (nodes x 3) indexed by the relabelled node number."""
     dim, k = {"tri": (2, 0), "tet": (3, 1), "hex": (3, 2)}[kind]
