@@ -52,21 +52,3 @@ def test_transient_steps_match_the_oracle(eh, which, solver):
         uo, ok, _, _ = oracle.cg(S, bo, x0=uo, rtol=1e-13)
         assert ok
     assert np.linalg.norm(uh - uo) <= 1e-8 * np.linalg.norm(uo)
-
-
-def test_warm_start_needs_fewer_iterations(eh):
-    K = gen.tet_lap3d(N=16)
-    c, S, R = _system(K)
-    PS, PR = eh.Plan(S), eh.Plan(R)
-    M = eh.Fsai(PS, S)
-    u = torch.from_numpy(gen.uniform(K.n, 6)).cuda()
-    b = torch.empty_like(u)
-    for _ in range(3):                    # a few steps: the iterate becomes smooth
-        PR.spmv(u, b)
-        PS.pcg(M, b, u, rtol=1e-10)
-    PR.spmv(u, b)
-    warm = u.clone()
-    _, iw = PS.pcg(M, b, warm, rtol=1e-10)
-    cold = torch.zeros_like(u)
-    _, ic = PS.pcg(M, b, cold, rtol=1e-10)
-    assert iw["iterations"] < ic["iterations"], (iw["iterations"], ic["iterations"])
