@@ -129,23 +129,41 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(
 constexpr int kBatch = 8;   // slots whose loads are issued before their FMAs (default batch depth)
 constexpr int kStage = 16;  // elements of x per thread in flight while a slice of x is gathered
 
-// acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory.  Loads are issued
-// KB at a time ahead of their FMAs; the FMAs run in slot order, so the result does not depend on KB.
-// (A predicated last batch measured slower than this scalar remainder on both 3D workloads.)
+// acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory.  Loads go out in
+// half-batches of KB/2 slots, the next half-batch issued before the current one's FMAs (KB slots held in
+// registers); the FMAs run in slot order, so the result does not depend on KB.  (A predicated last batch
+// measured slower than this scalar remainder on both 3D workloads.)
 template <typename V, typename X, int KB = kBatch>
 __device__ __forceinline__ X slab_dot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
                                       const X* xs, X acc, int lim, int32_t* status) {
+  constexpr int H = KB / 2;
   int k = 0;
-  for (; k + KB <= w; k += KB) {
-    X v[KB];
-    int c[KB];
+  if (w >= H) {
+    X va[H];
+    int ca[H];
 #pragma unroll
-    for (int u = 0; u < KB; ++u) {
-      v[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
-      c[u] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u))), lim, status);
+    for (int u = 0; u < H; ++u) {
+      va[u] = load_val<V, X>(vp + 32 * (int64_t)u);
+      ca[u] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)u)), lim, status);
+    }
+    for (k = H; k + H <= w; k += H) {
+      X vb[H];
+      int cb[H];
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        vb[u] = load_val<V, X>(vp + 32 * (int64_t)(k + u));
+        cb[u] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * (int64_t)(k + u))), lim, status);
+      }
+#pragma unroll
+      for (int u = 0; u < H; ++u) acc = fma_t(va[u], xs[ca[u]], acc);
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        va[u] = vb[u];
+        ca[u] = cb[u];
+      }
     }
 #pragma unroll
-    for (int u = 0; u < KB; ++u) acc = fma_t(v[u], xs[c[u]], acc);
+    for (int u = 0; u < H; ++u) acc = fma_t(va[u], xs[ca[u]], acc);
   }
   for (; k < w; ++k)
     acc = fma_t(load_val<V, X>(vp + 32 * (int64_t)k),
