@@ -691,6 +691,58 @@ def run_spmm(args):
     return 0
 
 
+def run_lowp(args):
+    """The low-precision SpMVs of the mixed-precision solvers (`ehyb_spmv_lowp`: FP32 or BF16 values, FP32 x, y,
+    FP32 accumulation, one fused launch) against the FP64 one on the same partition.  Algorithmic bytes per
+    SpMV: FP32 6 per slab entry (value + 16-bit column), 8 per ER entry, 4n (x) + 4n (y); BF16 4 / 6 per entry."""
+    import torch
+    import gen
+    import paper_2204_06666_gb300 as eh
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    w = WORKLOADS[args.workload]
+    A = make_matrix(w)
+    hbm, hbm_src = measured_peaks()
+    P32 = eh.Plan(A, lowp=1)
+    ex = P32.export()
+    pv = np.empty(A.n, np.int32)
+    for p in range(len(ex["part_ptr"]) - 1):
+        pv[ex["new_to_old"][ex["part_ptr"][p]:ex["part_ptr"][p + 1]]] = p
+    P16 = eh.Plan(A, lowp=2, part_vec=pv)
+    info = P32.info()
+    slab, er, n = info["ell_nnz"], info["er_nnz"], A.n
+    xh = gen.uniform(A.n, w["seed_x"])
+    x64 = torch.from_numpy(xh).cuda()
+    y64 = torch.empty_like(x64)
+    x32 = x64.float()
+    y32 = torch.empty_like(x32)
+    reps = max(50, args.steps // 10)
+    out = {}
+    for name, fn, nbytes in (("f64", lambda: P32.spmv(x64, y64), 10 * slab + 12 * er + 16 * n),
+                             ("f32", lambda: P32.spmv_lowp(x32, y32), 6 * slab + 8 * er + 8 * n),
+                             ("bf16", lambda: P16.spmv_lowp(x32, y32), 4 * slab + 6 * er + 8 * n)):
+        for _ in range(args.warmup):
+            fn()
+        t = _event_time(fn, reps, stream)
+        gbs = nbytes / t / 1e6
+        out[name] = {"us": t * 1e3, "gflops": 2.0 * A.nnz / t / 1e6, "bytes": nbytes, "gbs": gbs,
+                     "hbm_frac": gbs / hbm}
+    P32.spmv_lowp(x32, y32)
+    torch.cuda.synchronize()
+    y = y32.double().cpu().numpy()
+    P32.spmv(x64, y64)
+    torch.cuda.synchronize()
+    ref = y64.cpu().numpy()
+    line = {"metric": "EHYB low-precision SpMV effective GB/s (FP32 values, FP32 x/y)", "unit": "GB/s",
+            "value": out["f32"]["gbs"], "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "hbm_peak_gbs": hbm,
+                       "hbm_peak_source": hbm_src, "reps": reps},
+            "spmv": out,
+            "f32_vs_f64_rel_l2": float(np.linalg.norm(y - ref) / np.linalg.norm(ref))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _reorder(A, n2o, o2n):
     """P A P^T in CSR, rows in the plan numbering (columns relabelled, order kept)."""
     import gen
@@ -729,6 +781,7 @@ def main():
                     help="shared-memory budget per block of batched plans in bytes (caps partition rows; 0 = device max)")
     ap.add_argument("--spmm", action="store_true", help="time SpMM with --spmm-k right-hand sides")
     ap.add_argument("--spmm-k", type=int, nargs="+", default=[8, 32])
+    ap.add_argument("--lowp", action="store_true", help="time the FP32 / BF16 SpMVs of the mixed-precision solvers")
     ap.add_argument("--solver-reps", type=int, default=3)
     ap.add_argument("--transient", action="store_true",
                     help="time implicit-Euler steps (one plan and preconditioner, a PCG solve per step)")
@@ -747,6 +800,8 @@ def main():
         return run_batch(args)
     if args.spmm:
         return run_spmm(args)
+    if args.lowp:
+        return run_lowp(args)
     return run_ehyb(args)
 
 
