@@ -8,7 +8,8 @@
 //              {none, p99, p90 of the row lengths} x lanes per row in {1, 2, 4}: 63 configurations.
 //   sweep    : builds every configuration (host encodings in parallel threads, one partitioning per
 //              distinct partition size), uploads and times each one's ehyb_spmv on the GPU; the
-//              exhaustive answer, used as training data, as the fallback and as the judge.
+//              exhaustive answer, used as training data, as the fallback and as the yardstick of the
+//              learned choice.
 //   learned  : the MLP of mlp.cu (weights loaded with ehyb_tuner_set_model) maps normalised features to
 //              (log2 VecSize, cap index, log2 lanes, log time per entry); outputs snap to the grid.
 #include <algorithm>
