@@ -149,12 +149,11 @@ def cpu_baseline(A, x, budget_s: float = 10.0, y_gpu=None):
     return out
 
 
-KERNEL_SOURCES = ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu",
-                  "paper_2204_06666_gb300/csrc/plan.cpp", "paper_2204_06666_gb300/csrc/partition_ml.cpp")
+KERNEL_SOURCES = ("paper_2204_06666_gb300/csrc/ehyb_core.cuh", "paper_2204_06666_gb300/csrc/spmv_kernels.cu")
 
 
 def kernel_source_sha() -> str:
-    """Hash of the sources that decide the fused kernel's memory traffic (kernel body, launch, layout)."""
+    """Hash of the sources of the fused kernel and its launch."""
     import hashlib
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
@@ -163,16 +162,21 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str):
+def layout_signature(info: dict) -> str:
+    """The plan's byte layout as the kernel reads it: partitions, slices, stored slab and ER slots, ER entries."""
+    return "/".join(str(info[k]) for k in ("nparts", "nslices", "ell_stored", "er_stored", "er_nnz"))
+
+
+def recorded_traffic(workload: str, layout: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu capture, or None when the kernel's
-    sources changed since the capture (or no capture exists for this workload)."""
+    sources or the plan's layout differ from the captured ones (or no capture exists for this workload)."""
     p = os.path.join(ROOT, "profiles", "ehyb_kernel_dram.json")
     if not os.path.exists(p):
         return None, None
     with open(p) as f:
         rec = json.load(f)
     r = rec.get(workload)
-    if not r or r.get("source_sha") != kernel_source_sha():
+    if not r or r.get("source_sha") != kernel_source_sha() or r.get("layout") != layout:
         return None, None
     return float(r["dram_bytes_per_launch"]), r.get("note")
 
@@ -314,7 +318,8 @@ def run_ehyb(args):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": None, "peak_source": f"{peak_src} copy bandwidth",
                 "alu": {"achieved": fp64_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak}}
-    traffic, tnote = recorded_traffic(args.workload + ("_multilevel" if args.partitioner else ""))
+    traffic, tnote = recorded_traffic(args.workload + ("_multilevel" if args.partitioner else ""),
+                                      layout_signature(info))
     roof["traffic"] = traffic
     if traffic is not None:
         roof["traffic_over_algorithmic"] = traffic / bytes_alg

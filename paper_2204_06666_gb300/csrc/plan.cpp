@@ -91,10 +91,17 @@ void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads
     for (int64_t i = lo; i < hi; ++i) {
       int32_t* b = tmp.get() + rp[i];
       int64_t m = 0;
+      bool increasing = true;  // rows stored with strictly increasing columns need no sort
       for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
-        if (col[k] != i) b[m++] = col[k];
-      std::sort(b, b + m);
-      len[(size_t)i + 1] = std::unique(b, b + m) - b;
+        if (col[k] != i) {
+          increasing = increasing && (m == 0 || col[k] > b[m - 1]);
+          b[m++] = col[k];
+        }
+      if (!increasing) {
+        std::sort(b, b + m);
+        m = std::unique(b, b + m) - b;
+      }
+      len[(size_t)i + 1] = m;
     }
   });
   // the pattern is symmetric when the multiset of its edges (i, c) equals that of (c, i): compared

@@ -44,8 +44,9 @@ def test_aggregate_single_rank():
     assert bench.aggregate(100.0, 1, 5e8) == (5e8 / 0.1, 100.0)
 
 
-def test_traffic_record_tied_to_kernel_sources(tmp_path, monkeypatch):
-    rec = {"hex_elast3d_70": {"source_sha": bench.kernel_source_sha(), "dram_bytes_per_launch": 9.0e8,
+def test_traffic_record_tied_to_kernel_sources_and_layout(tmp_path, monkeypatch):
+    lay = "152/32208/411238400/12930000/11921367"
+    rec = {"hex_elast3d_70": {"source_sha": bench.kernel_source_sha(), "layout": lay, "dram_bytes_per_launch": 9.0e8,
                               "note": "x"}}
     prof = tmp_path / "profiles"
     prof.mkdir()
@@ -56,10 +57,13 @@ def test_traffic_record_tied_to_kernel_sources(tmp_path, monkeypatch):
         dst = tmp_path / rel
         dst.parent.mkdir(parents=True, exist_ok=True)
         dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
-    assert bench.recorded_traffic("hex_elast3d_70")[0] == 9.0e8
-    assert bench.recorded_traffic("fem2d_p1_200")[0] is None
+    assert bench.recorded_traffic("hex_elast3d_70", lay)[0] == 9.0e8
+    assert bench.recorded_traffic("fem2d_p1_200", lay)[0] is None
+    assert bench.recorded_traffic("hex_elast3d_70", "152/1/2/3/4")[0] is None     # another plan layout
     (tmp_path / "paper_2204_06666_gb300/csrc/ehyb_core.cuh").write_text("// changed kernel")
-    assert bench.recorded_traffic("hex_elast3d_70")[0] is None     # kernel changed: no stale traffic
+    assert bench.recorded_traffic("hex_elast3d_70", lay)[0] is None                # kernel changed: no stale traffic
+    info = {"nparts": 152, "nslices": 32208, "ell_stored": 411238400, "er_stored": 12930000, "er_nnz": 11921367}
+    assert bench.layout_signature(info) == lay
 
 
 def test_reference_arm_line():
