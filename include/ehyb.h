@@ -267,7 +267,8 @@ ehyb_status_t ehyb_precond_info(ehyb_precond_t M, int64_t* nnz_g, double* setup_
 /* G in the plan's numbering (host CSR, rows sorted; valid until ehyb_precond_destroy) */
 ehyb_status_t ehyb_precond_export(ehyb_precond_t M, int64_t* n, const int64_t** row_ptr, const int32_t** col,
                                   const double** val);
-ehyb_status_t ehyb_precond_destroy(ehyb_precond_t M); /* NULL is fine; synchronises the device */
+ehyb_status_t ehyb_precond_destroy(ehyb_precond_t M); /* NULL is fine; synchronises the device when M holds
+                                                         device memory; M is freed whatever the status */
 
 /*
  * Preconditioned CG on `plan` with M (built for this plan): x (device, caller's numbering) holds x0 on

@@ -300,8 +300,8 @@ class Plan:
 
     def close(self):
         if self._h:
-            _check(_lib.ehyb_destroy(self._h), "ehyb_destroy")
-            self._h = ctypes.c_void_p()
+            h, self._h = self._h, ctypes.c_void_p()   # the handle is released whatever the status
+            _check(_lib.ehyb_destroy(h), "ehyb_destroy")
 
     def __del__(self):
         try:
@@ -458,8 +458,8 @@ class Fsai:
 
     def close(self):
         if self._h:
-            _check(_lib.ehyb_precond_destroy(self._h), "ehyb_precond_destroy")
-            self._h = ctypes.c_void_p()
+            h, self._h = self._h, ctypes.c_void_p()   # the handle is released whatever the status
+            _check(_lib.ehyb_precond_destroy(h), "ehyb_precond_destroy")
 
     def __del__(self):
         try:
@@ -490,8 +490,8 @@ class CsrBaseline:
 
     def close(self):
         if self._h:
-            _check(_lib.ehyb_csr_destroy(self._h), "ehyb_csr_destroy")
-            self._h = ctypes.c_void_p()
+            h, self._h = self._h, ctypes.c_void_p()   # the handle is released whatever the status
+            _check(_lib.ehyb_csr_destroy(h), "ehyb_csr_destroy")
 
     def __del__(self):
         try:
@@ -523,8 +523,8 @@ class Batch:
 
     def close(self):
         if self._h:
-            _check(_lib.ehyb_batch_destroy(self._h), "ehyb_batch_destroy")
-            self._h = ctypes.c_void_p()
+            h, self._h = self._h, ctypes.c_void_p()   # the handle is released whatever the status
+            _check(_lib.ehyb_batch_destroy(h), "ehyb_batch_destroy")
 
     def __del__(self):
         try:

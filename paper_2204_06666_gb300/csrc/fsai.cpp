@@ -97,17 +97,22 @@ extern "C" ehyb_status_t ehyb_fsai_create(ehyb_plan_t plan, int64_t n, int64_t n
   try {
     M.reset(new ehyb_precond_s());
     M->rp.assign((size_t)n + 1, 0);
-    for (int64_t r = 0; r < n; ++r) {
-      int64_t m = 0;
-      bool diag = false;
-      for (int64_t k = brp[(size_t)r]; k < brp[(size_t)r + 1] && bcol[(size_t)k] <= r; ++k) {
-        ++m;
-        diag = diag || bcol[(size_t)k] == r;
+    std::atomic<int> too_large{0};
+    parallel_for(n, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t r = lo; r < hi; ++r) {
+        int64_t m = 0;
+        bool diag = false;
+        for (int64_t k = brp[(size_t)r]; k < brp[(size_t)r + 1] && bcol[(size_t)k] <= r; ++k) {
+          ++m;
+          diag = diag || bcol[(size_t)k] == r;
+        }
+        if (!diag) ++m;
+        if (m > kMaxBlock) too_large.store(1, std::memory_order_relaxed);
+        M->rp[(size_t)r + 1] = m;
       }
-      if (!diag) ++m;
-      if (m > kMaxBlock) return EHYB_ERR_TOO_LARGE;
-      M->rp[(size_t)r + 1] = M->rp[(size_t)r] + m;
-    }
+    });
+    if (too_large.load()) return EHYB_ERR_TOO_LARGE;
+    for (int64_t r = 0; r < n; ++r) M->rp[(size_t)r + 1] += M->rp[(size_t)r];
     M->col.resize((size_t)M->rp[(size_t)n]);
     M->val.resize((size_t)M->rp[(size_t)n]);
   } catch (const std::bad_alloc&) {
@@ -166,19 +171,57 @@ extern "C" ehyb_status_t ehyb_fsai_create(ehyb_plan_t plan, int64_t n, int64_t n
   const double t2 = now_ms();
 
   // G^T (rows = columns of G), then the two plans on the matrix plan's partition
-  std::vector<int64_t> trp((size_t)n + 1, 0);
-  std::vector<int32_t> tcol(M->col.size());
-  std::vector<double> tval(M->val.size());
-  for (int32_t c : M->col) ++trp[(size_t)c + 1];
-  for (int64_t r = 0; r < n; ++r) trp[(size_t)r + 1] += trp[(size_t)r];
-  {
-    std::vector<int64_t> fill(trp.begin(), trp.end() - 1);
-    for (int64_t r = 0; r < n; ++r)
-      for (int64_t k = M->rp[(size_t)r]; k < M->rp[(size_t)r + 1]; ++k) {
-        const int64_t pos = fill[(size_t)M->col[(size_t)k]]++;
-        tcol[(size_t)pos] = (int32_t)r;
-        tval[(size_t)pos] = M->val[(size_t)k];
+  // counting transpose on T row blocks: each block counts its columns, the offsets of column c are laid
+  // out block after block, so every row of G^T lists its entries in increasing row of G (the serial order)
+  std::vector<int64_t> trp;
+  std::vector<int32_t> tcol;
+  std::vector<double> tval;
+  try {
+    trp.assign((size_t)n + 1, 0);
+    tcol.resize(M->col.size());
+    tval.resize(M->val.size());
+    const int64_t TB = std::max<int64_t>(1, std::min<int64_t>(std::min(T, 8), n / 65536 + 1));  // <= 8 count arrays
+    std::vector<std::vector<int64_t>> cnt((size_t)TB);
+    parallel_for(TB, (int)TB, [&](int64_t b0, int64_t b1) {
+      for (int64_t b = b0; b < b1; ++b) {
+        std::vector<int64_t>& c = cnt[(size_t)b];
+        c.assign((size_t)n, 0);
+        for (int64_t r = n * b / TB; r < n * (b + 1) / TB; ++r)
+          for (int64_t k = M->rp[(size_t)r]; k < M->rp[(size_t)r + 1]; ++k) ++c[(size_t)M->col[(size_t)k]];
       }
+    }, 1);
+    // cnt[b][c] becomes block b's first position in row c of G^T
+    parallel_for(n, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t c = lo; c < hi; ++c) {
+        int64_t tot = 0;
+        for (int64_t b = 0; b < TB; ++b) tot += cnt[(size_t)b][(size_t)c];
+        trp[(size_t)c + 1] = tot;
+      }
+    });
+    for (int64_t r = 0; r < n; ++r) trp[(size_t)r + 1] += trp[(size_t)r];
+    parallel_for(n, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t c = lo; c < hi; ++c) {
+        int64_t at = trp[(size_t)c];
+        for (int64_t b = 0; b < TB; ++b) {
+          const int64_t k = cnt[(size_t)b][(size_t)c];
+          cnt[(size_t)b][(size_t)c] = at;
+          at += k;
+        }
+      }
+    });
+    parallel_for(TB, (int)TB, [&](int64_t b0, int64_t b1) {
+      for (int64_t b = b0; b < b1; ++b) {
+        std::vector<int64_t>& fill = cnt[(size_t)b];
+        for (int64_t r = n * b / TB; r < n * (b + 1) / TB; ++r)
+          for (int64_t k = M->rp[(size_t)r]; k < M->rp[(size_t)r + 1]; ++k) {
+            const int64_t pos = fill[(size_t)M->col[(size_t)k]]++;
+            tcol[(size_t)pos] = (int32_t)r;
+            tval[(size_t)pos] = M->val[(size_t)k];
+          }
+      }
+    }, 1);
+  } catch (const std::bad_alloc&) {
+    return EHYB_ERR_OOM;
   }
   std::vector<int32_t> pv((size_t)n);
   for (int32_t p = 0; p < H.nparts; ++p)
@@ -224,10 +267,15 @@ extern "C" ehyb_status_t ehyb_precond_export(ehyb_precond_t M, int64_t* n, const
 
 extern "C" ehyb_status_t ehyb_precond_destroy(ehyb_precond_t M) {
   if (!M) return EHYB_OK;
-  cudaError_t e = cudaDeviceSynchronize();
-  if (M->work) pcg_work_free(M->work);
-  ehyb_destroy(M->g);
-  ehyb_destroy(M->gt);
-  delete M;
-  return e == cudaSuccess ? EHYB_OK : cuda_error_status(e, "cudaDeviceSynchronize");
+  // a preconditioner of a host-only plan holds no device memory: nothing to wait for
+  cudaError_t e = cudaSuccess;
+  if (M->work) {
+    e = cudaDeviceSynchronize();
+    pcg_work_free(M->work);
+  }
+  ehyb_status_t st = ehyb_destroy(M->g);
+  const ehyb_status_t st2 = ehyb_destroy(M->gt);
+  delete M;  // freed whatever the status: the handle is invalid after this call
+  if (e != cudaSuccess) return cuda_error_status(e, "cudaDeviceSynchronize");
+  return st != EHYB_OK ? st : st2;
 }

@@ -43,3 +43,16 @@ def test_not_spd_is_refused(eh):
     with pytest.raises(eh.EhybError) as e:
         eh.Fsai(P, N)
     assert e.value.status == 1
+
+
+def test_host_only_preconditioner_closes_without_a_device():
+    # a host-only plan's preconditioner holds no device memory: releasing it must not touch CUDA, and the
+    # handle is gone after the first close (a second close and the destructor do nothing)
+    import paper_2204_06666_gb300 as eh
+    A = gen.tet_lap3d(N=6)
+    P = eh.Plan(A, host_only=1, num_sms=4)
+    M = eh.Fsai(P, A)
+    M.close()
+    M.close()
+    P.close()
+    P.close()
