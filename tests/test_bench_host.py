@@ -73,3 +73,17 @@ def test_reference_arm_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "GFLOP/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_cpu_baselines_compute_the_product():
+    # the single-thread sample and the all-core run use the oracle's row routine; the all-core run's rows
+    # together are one whole product
+    import numpy as np
+    import gen
+    import oracle
+    A = gen.fem2d_p1(N=60)
+    x = gen.uniform(A.n, 3)
+    one = bench.cpu_baseline(A, x, 0.2, oracle.spmv(A, x))
+    assert one["value"] > 0 and one["cores"] == 1 and one["parity"]["rel_l2"] == 0.0
+    multi = one["multicore"]
+    assert multi["value"] > 0 and multi["cores"] >= 1 and multi["kind"] == "oracle"
