@@ -1,20 +1,24 @@
-// Multilevel recursive bisection for the planner's PartVec (Sec. 3.1 cuts the graph of A with METIS's
-// multilevel scheme; this is the Karypis-Kumar scheme written from its published description):
+// Multilevel partitioner for the planner's PartVec (Sec. 3.1 cuts the graph of A with METIS's multilevel
+// scheme; this is the Karypis-Kumar scheme written from its published description):
 //
 //   * the graph: one vertex per supervariable (weight = its rows), an edge wherever two supervariables'
 //     rows are adjacent in A + A^T, weighted by the entries it stands for (the product of the two row
-//     counts), so the cut weight is the count of entries that leave their partition (the ER entries);
-//   * each bisection of a graph destined for k parts coarsens it by heavy-edge matching (vertices visited
-//     in a seeded random order, each paired with the free neighbour across its heaviest edge), bisects
-//     the coarsest graph by greedy graph growing (several seeds, the smallest cut kept), and projects the
-//     bisection back level by level, improving it with Fiduccia-Mattheyses passes (boundary vertices
-//     moved by largest cut reduction, the best prefix of each pass kept);
-//   * the two sides get floor(k/2) and ceil(k/2) parts and exactly their share of the rows: after the
-//     finest level, vertices leave the heavy side by largest gain until the weights are exact, the last
-//     one split when it is heavier than what is left to move (a supervariable can straddle two parts,
-//     as in the greedy partitioner), so every part ends with at most `cap` rows;
-//   * the two halves are bisected in parallel; every step depends only on its own subgraph and seed, so
-//     the result does not depend on the thread count.
+//     counts), so the cut weight is the count of entries that leave their partition (the ER entries); it
+//     is renumbered breadth-first so that every later pass walks memory locally;
+//   * coarsening, once for the whole graph: heavy-edge matching (vertices visited in seeded-shuffled blocks
+//     of the numbering, each paired with the free neighbour across its heaviest edge), until about 20
+//     vertices per part remain;
+//   * initial partition of the coarsest graph into k = ceil(n / cap) parts by recursive bisection, each
+//     bisection itself multilevel: heavy-edge coarsening, greedy graph growing from several seeds, and
+//     Fiduccia-Mattheyses passes (boundary vertices moved by largest cut reduction, the best prefix of each
+//     pass kept) on the way back up; the two halves run in parallel;
+//   * uncoarsening with greedy k-way refinement: boundary vertices move to the adjacent part that gains the
+//     most cut weight while parts stay within 3 % of the mean;
+//   * exact part sizes, top-down over the bisection tree of part ids: at each node the heavy half gives its
+//     best-gain boundary vertices to the light half until the left half holds exactly its share of the rows,
+//     the last vertex split when it is heavier than what is left (a supervariable can straddle two parts,
+//     as in the greedy partitioner), so every part ends with at most `cap` rows.
+// Every step depends only on its input and the seed, so the result does not depend on the thread count.
 #include <algorithm>
 #include <cstdlib>
 #include <thread>
