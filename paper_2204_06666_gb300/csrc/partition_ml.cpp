@@ -356,13 +356,13 @@ void coarsen(const Graph& g, int64_t maxvw, Rng& r, int threads, Graph& c, std::
   // coarse lists: the union of the pair's lists, weights of parallel edges summed, self edges dropped
   const int64_t t = std::max<int64_t>(1, std::min<int64_t>(threads, (nc + 16383) / 16384));
   std::vector<std::vector<int64_t>> slots((size_t)t);  // per worker: position of a coarse neighbour in its list
-  build_lists(nc, (int)t, c, [&](int64_t cv, int64_t k, std::vector<int32_t>& a, std::vector<int64_t>& w) {
-    std::vector<int64_t>& slot = slots[(size_t)k];
+  build_lists(nc, (int)t, c, [&](int64_t cv, int64_t worker, std::vector<int32_t>& a, std::vector<int64_t>& w) {
+    std::vector<int64_t>& slot = slots[(size_t)worker];
     if (slot.empty()) slot.assign((size_t)nc, -1);
     const int64_t begin = (int64_t)a.size();
     const int32_t pair[2] = {rep[(size_t)cv], match[(size_t)rep[(size_t)cv]]};
-    for (int k = 0; k < (pair[1] == pair[0] ? 1 : 2); ++k) {
-      const int32_t f = pair[k];
+    for (int h = 0; h < (pair[1] == pair[0] ? 1 : 2); ++h) {
+      const int32_t f = pair[h];
       for (int64_t e = g.xadj[(size_t)f]; e < g.xadj[(size_t)f + 1]; ++e) {
         const int32_t cu = cmap[(size_t)g.adj[(size_t)e]];
         if (cu == cv) continue;
