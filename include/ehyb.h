@@ -185,6 +185,17 @@ ehyb_status_t ehyb_permute(ehyb_plan_t plan, int32_t to_new, const double* in, d
 ehyb_status_t ehyb_spmv_host(ehyb_plan_t plan, const double* x_host, double* y_host, void* stream);
 
 /*
+ * y_i = A x_i for `count` pairs of HOST vectors (x_host[i], y_host[i]: n doubles each), pipelined: the copy
+ * of x_{i+1} into the device and the copy of y_{i-1} out of it overlap the product of step i (two device
+ * buffer pairs; the copies run on two streams of the plan's own, the products on `stream`).  Every y_i is
+ * on the host when the call returns; each equals ehyb_spmv's result bit for bit.  Host memory should be
+ * pinned (pageable memory works, without the overlap).  NULL arrays or entries give EHYB_ERR_INVALID_ARG;
+ * count 0 does nothing.
+ */
+ehyb_status_t ehyb_spmv_host_many(ehyb_plan_t plan, int32_t count, const double* const* x_host,
+                                  double* const* y_host, void* stream);
+
+/*
  * y = A x exactly as ehyb_spmv computes it, for callers that cannot allocate device memory when
  * they call (a plug-in whose host framework owns all device memory, a latency-critical loop, a
  * thread holding a lock the allocator needs).  The paper has no counterpart: this is a library

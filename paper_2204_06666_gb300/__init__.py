@@ -109,6 +109,7 @@ _sig("ehyb_spmv", [_P, _P, _P, _P])
 _sig("ehyb_spmv_permuted", [_P, _P, _P, _P])
 _sig("ehyb_permute", [_P, _I32, _P, _P, _P])
 _sig("ehyb_spmv_host", [_P, _P, _P, _P])
+_sig("ehyb_spmv_host_many", [_P, _I32, _P, _P, _P])
 _sig("ehyb_spmv_lowp", [_P, _P, _P, _P])
 _sig("ehyb_spmv_noalloc", [_P, _P, _P, _P])
 _sig("ehyb_spmm", [_P, _I32, _P, _P, _P])
@@ -177,8 +178,8 @@ def _dev(t, dtype_name: str) -> int:
 
 def _host(a, dtype) -> int:
     if hasattr(a, "data_ptr") and not hasattr(a, "ctypes"):  # torch CPU tensor (possibly pinned)
-        if a.is_cuda or not a.is_contiguous():
-            raise TypeError("expected a contiguous CPU tensor")
+        if a.is_cuda or not a.is_contiguous() or a.element_size() != np.dtype(dtype).itemsize:
+            raise TypeError(f"expected a contiguous CPU tensor of {np.dtype(dtype)}")
         return a.data_ptr()
     if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
         raise TypeError(f"expected a contiguous numpy {np.dtype(dtype)} array")
@@ -324,6 +325,14 @@ class Plan:
     def spmv_host(self, x, y, stream=None):
         _check(ehyb_spmv_host(self._h, _host(x, np.float64), _host(y, np.float64), _stream(stream)),
                "ehyb_spmv_host")
+
+    def spmv_host_many(self, xs, ys, stream=None):
+        """y_i = A x_i for lists of CPU float64 tensors (pinned for overlap), copies and products pipelined."""
+        if len(xs) != len(ys):
+            raise ValueError("xs and ys differ in length")
+        X = (ctypes.c_void_p * max(1, len(xs)))(*[_host(x, np.float64) for x in xs])
+        Y = (ctypes.c_void_p * max(1, len(ys)))(*[_host(y, np.float64) for y in ys])
+        _check(_lib.ehyb_spmv_host_many(self._h, len(xs), X, Y, _stream(stream)), "ehyb_spmv_host_many")
 
     def spmv_lowp(self, x, y, stream=None):
         _check(ehyb_spmv_lowp(self._h, _dev(x, "float32"), _dev(y, "float32"), _stream(stream)), "ehyb_spmv_lowp")

@@ -472,12 +472,21 @@ extern "C" {
 ehyb_status_t ehyb_destroy(ehyb_plan_t p) {
   if (!p) return EHYB_OK;
   ehyb_status_t st = EHYB_OK;
-  if (p->arena || p->hx || p->cg || p->spmm_ws || !p->ev_pool.empty()) {
+  if (p->arena || p->hx || p->cg || p->spmm_ws || !p->ev_pool.empty() || p->px[0] || p->s_in) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
     if (p->arena) cudaFree(p->arena);
     if (p->hx) cudaFree(p->hx);
     if (p->hy) cudaFree(p->hy);
+    for (int b = 0; b < 2; ++b) {
+      if (p->px[b]) cudaFree(p->px[b]);
+      if (p->py[b]) cudaFree(p->py[b]);
+      if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
+      if (p->ev_k[b]) cudaEventDestroy(p->ev_k[b]);
+      if (p->ev_out[b]) cudaEventDestroy(p->ev_out[b]);
+    }
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
     if (p->cg) cg_work_free(p->cg);
     if (p->spmm_ws) cudaFree(p->spmm_ws);
     for (auto& ev : p->ev_pool) {
@@ -567,6 +576,45 @@ ehyb_status_t ehyb_spmv_host(ehyb_plan_t p, const double* xh, double* yh, void* 
   CK(cudaMemcpyAsync(p->hx, xh, bytes, cudaMemcpyHostToDevice, s));
   if ((st = ehyb_spmv(p, p->hx, p->hy, stream)) != EHYB_OK) return st;
   CK(cudaMemcpyAsync(yh, p->hy, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return EHYB_OK;
+}
+
+ehyb_status_t ehyb_spmv_host_many(ehyb_plan_t p, int32_t count, const double* const* xh, double* const* yh,
+                                  void* stream) {
+  ehyb_status_t st = check_run(p);
+  if (st != EHYB_OK) return st;
+  if (count < 0 || (count > 0 && (!xh || !yh))) return EHYB_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < count; ++i)
+    if (!xh[i] || !yh[i]) return EHYB_ERR_INVALID_ARG;
+  if (p->dev.n == 0 || count == 0) return EHYB_OK;
+  const size_t bytes = (size_t)p->dev.n * sizeof(double);
+  if (!p->s_in) {  // first use: two buffer pairs, two copy streams, six events
+    for (int b = 0; b < 2; ++b) {
+      if ((st = dev_alloc((void**)&p->px[b], bytes)) != EHYB_OK) return st;
+      if ((st = dev_alloc((void**)&p->py[b], bytes)) != EHYB_OK) return st;
+      CK(cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&p->ev_k[b], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&p->ev_out[b], cudaEventDisableTiming));
+    }
+    CK(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int32_t i = 0; i < count; ++i) {
+    const int b = i & 1;
+    if (i >= 2) CK(cudaStreamWaitEvent(p->s_in, p->ev_k[b], 0));  // product i-2 has read px[b]
+    CK(cudaMemcpyAsync(p->px[b], xh[i], bytes, cudaMemcpyHostToDevice, p->s_in));
+    CK(cudaEventRecord(p->ev_in[b], p->s_in));
+    CK(cudaStreamWaitEvent(s, p->ev_in[b], 0));
+    if (i >= 2) CK(cudaStreamWaitEvent(s, p->ev_out[b], 0));  // y of step i-2 has left py[b]
+    if ((st = ehyb_spmv(p, p->px[b], p->py[b], stream)) != EHYB_OK) return st;
+    CK(cudaEventRecord(p->ev_k[b], s));
+    CK(cudaStreamWaitEvent(p->s_out, p->ev_k[b], 0));
+    CK(cudaMemcpyAsync(yh[i], p->py[b], bytes, cudaMemcpyDeviceToHost, p->s_out));
+    CK(cudaEventRecord(p->ev_out[b], p->s_out));
+  }
+  CK(cudaStreamSynchronize(p->s_out));
   CK(cudaStreamSynchronize(s));
   return EHYB_OK;
 }

@@ -37,6 +37,12 @@ struct ehyb_plan_s {
   float* xp32 = nullptr;    // FP32 workspace
   double* hx = nullptr;     // device staging for ehyb_spmv_host
   double* hy = nullptr;
+  // pipelined host entry (ehyb_spmv_host_many): two device x / y pairs, copy-in and copy-out streams,
+  // and per buffer the events "x copied in", "product done", "y copied out"
+  double* px[2] = {nullptr, nullptr};
+  double* py[2] = {nullptr, nullptr};
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   int32_t lowp = 0;
   int32_t er_tpr = 1;
   int32_t er_layout = 0;

@@ -211,6 +211,30 @@ def test_host_entry_matches_device_entry(eh):
     assert np.array_equal(yn, y)
 
 
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_pipelined_host_entry_matches_device_entry(eh, count):
+    # x_{i+1} in and y_{i-1} out overlap product i; each result must equal the device entry's bits
+    A = gen.hex_elast3d(N=12)
+    P = eh.Plan(A)
+    xs = [torch.from_numpy(gen.uniform(A.n, 40 + i)).pin_memory() for i in range(count)]
+    ys = [torch.full((A.n,), np.nan, dtype=torch.float64).pin_memory() for _ in range(count)]
+    P.spmv_host_many(xs, ys)
+    for i in range(count):
+        xd = xs[i].cuda()
+        yd = torch.empty_like(xd)
+        P.spmv(xd, yd)
+        torch.cuda.synchronize()
+        assert np.array_equal(ys[i].numpy(), yd.cpu().numpy()), i
+        _check_fp(A, xs[i].numpy(), ys[i].numpy())
+    outs = [torch.empty_like(xs[0]).pin_memory() for _ in range(3)]
+    P.spmv_host_many([xs[0]] * 3, outs)                                # one input three times
+    assert all(np.array_equal(o.numpy(), outs[0].numpy()) for o in outs)
+    P.spmv_host_many([], [])                                            # count 0: nothing to do
+    import ctypes
+    null = (ctypes.c_void_p * 1)(None)
+    assert eh._lib.ehyb_spmv_host_many(P._h, 1, null, null, None) == 1  # a NULL entry: EHYB_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("lowp", [1, 2])
 def test_lowp_integer_exact_and_fem_bound(eh, lowp):
     A = gen.random_csr(2000, 4, mean_row=12, int_values=True, empty_frac=0.05, long_rows=2, long_len=600)
