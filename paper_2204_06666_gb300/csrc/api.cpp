@@ -574,7 +574,10 @@ ehyb_status_t ehyb_spmv_host(ehyb_plan_t p, const double* xh, double* yh, void* 
   }
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(p->hx, xh, bytes, cudaMemcpyHostToDevice, s));
-  if ((st = ehyb_spmv(p, p->hx, p->hy, stream)) != EHYB_OK) return st;
+  if ((st = ehyb_spmv(p, p->hx, p->hy, stream)) != EHYB_OK) {
+    (void)cudaStreamSynchronize(s);  // the copy of x has finished reading the caller's buffer
+    return st;
+  }
   CK(cudaMemcpyAsync(yh, p->hy, bytes, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return EHYB_OK;
@@ -601,21 +604,31 @@ ehyb_status_t ehyb_spmv_host_many(ehyb_plan_t p, int32_t count, const double* co
     CK(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
   }
   cudaStream_t s = (cudaStream_t)stream;
-  for (int32_t i = 0; i < count; ++i) {
+  // one step's enqueues; on a failure every stream is drained before returning, so no copy is still in
+  // flight to or from the caller's host buffers
+  auto step = [&](int32_t i) -> ehyb_status_t {
     const int b = i & 1;
     if (i >= 2) CK(cudaStreamWaitEvent(p->s_in, p->ev_k[b], 0));  // product i-2 has read px[b]
     CK(cudaMemcpyAsync(p->px[b], xh[i], bytes, cudaMemcpyHostToDevice, p->s_in));
     CK(cudaEventRecord(p->ev_in[b], p->s_in));
     CK(cudaStreamWaitEvent(s, p->ev_in[b], 0));
     if (i >= 2) CK(cudaStreamWaitEvent(s, p->ev_out[b], 0));  // y of step i-2 has left py[b]
-    if ((st = ehyb_spmv(p, p->px[b], p->py[b], stream)) != EHYB_OK) return st;
+    const ehyb_status_t r = ehyb_spmv(p, p->px[b], p->py[b], stream);
+    if (r != EHYB_OK) return r;
     CK(cudaEventRecord(p->ev_k[b], s));
     CK(cudaStreamWaitEvent(p->s_out, p->ev_k[b], 0));
     CK(cudaMemcpyAsync(yh[i], p->py[b], bytes, cudaMemcpyDeviceToHost, p->s_out));
     CK(cudaEventRecord(p->ev_out[b], p->s_out));
-  }
-  CK(cudaStreamSynchronize(p->s_out));
-  CK(cudaStreamSynchronize(s));
+    return EHYB_OK;
+  };
+  for (int32_t i = 0; i < count && st == EHYB_OK; ++i) st = step(i);
+  const cudaError_t e1 = cudaStreamSynchronize(p->s_in);
+  const cudaError_t e2 = cudaStreamSynchronize(p->s_out);
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (st != EHYB_OK) return st;
+  if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamSynchronize");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
   return EHYB_OK;
 }
 
