@@ -387,6 +387,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
   std::vector<int64_t> next_row((size_t)nv);  // first unassigned row of each (new) vertex
   for (int64_t v = 0; v < nv; ++v) next_row[(size_t)v] = first[(size_t)label[(size_t)v]];
   std::vector<char> done((size_t)nv, 0);
+  std::vector<int32_t> done_nb((size_t)nv, 0);  // assigned neighbours of each vertex, kept up to date
   int64_t cursor = 0, assigned = 0;
   auto next_free = [&]() -> int32_t {
     while (cursor < nv && done[(size_t)order[(size_t)cursor]]) ++cursor;
@@ -409,6 +410,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       members.push_back(v);
       for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
         int32_t u = ga[(size_t)e];
+        ++done_nb[(size_t)u];
         if (done[(size_t)u]) continue;
         if (conn[(size_t)u] == 0) touched.push_back(u);
         q.raise(u, ++conn[(size_t)u]);
@@ -434,8 +436,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
           int32_t u = ga[(size_t)e];
           if (done[(size_t)u] || stamp[(size_t)u] == p) continue;
           stamp[(size_t)u] = p;
-          int64_t a = 0;
-          for (int64_t f = gx[(size_t)u]; f < gx[(size_t)u + 1]; ++f) a += done[(size_t)ga[(size_t)f]] != 0;
+          const int64_t a = done_nb[(size_t)u];
           if (a > best) { best = a; seed = u; }
         }
     }
