@@ -201,12 +201,20 @@ int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::v
     }
     return true;
   };
+  // a run breaks before row i unless rows i-1 and i have equal closed neighbourhoods (an equivalence, so
+  // comparing neighbours in row order finds the same runs as comparing with each run's first row); the
+  // comparisons are independent and run in parallel
+  std::vector<uint8_t> brk((size_t)n);
+  parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      brk[(size_t)i] = i == 0 || key[(size_t)i] != key[(size_t)i - 1] || !same((int32_t)(i - 1), (int32_t)i);
+  });
   sv_of.assign((size_t)n, 0);
   first.clear();
   first.reserve((size_t)n + 1);
   int64_t nsv = 0;
   for (int64_t i = 0; i < n; ++i) {
-    if (i == 0 || key[(size_t)i] != key[(size_t)i - 1] || !same((int32_t)first.back(), (int32_t)i)) {
+    if (brk[(size_t)i]) {
       first.push_back(i);
       ++nsv;
     }
