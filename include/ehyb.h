@@ -92,8 +92,9 @@ typedef struct {
   int32_t partitioner;       /* PartVec when part_vec is NULL (Sec. 3.1): 0 = greedy graph growing (default),
                                 1 = multilevel recursive bisection (heavy-edge coarsening, greedy-growing initial
                                 bisection, Fiduccia-Mattheyses refinement; ceil(n / slice_rows) parts of equal
-                                size); other values give EHYB_ERR_INVALID_ARG.  The exhaustive sweep (tuner 2)
-                                times greedy-growing partitions only */
+                                size; more than 16,384 parts fall back to greedy growing); other values give
+                                EHYB_ERR_INVALID_ARG.  The exhaustive sweep (tuner 2) times greedy-growing
+                                partitions only */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;

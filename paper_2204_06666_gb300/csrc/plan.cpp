@@ -474,8 +474,12 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     part.assign(prm.part_vec, prm.part_vec + n);
     for (int64_t i = 0; i < n; ++i) nparts = std::max(nparts, part[(size_t)i] + 1);
   } else {
-    nparts = prm.partitioner == 1 ? partition_multilevel(n, rp, col, prm.slice_rows, prm.seed, part, prm.threads)
-                                  : partition_graph(n, rp, col, prm.slice_rows, part, prm.threads);
+    // the multilevel scheme is meant for parts on the order of the SM count; for very many tiny parts
+    // (more than kMaxMultilevelParts) greedy growing is used instead
+    const int64_t want = prm.slice_rows > 0 ? (n + prm.slice_rows - 1) / prm.slice_rows : n;
+    nparts = prm.partitioner == 1 && want <= kMaxMultilevelParts
+                 ? partition_multilevel(n, rp, col, prm.slice_rows, prm.seed, part, prm.threads)
+                 : partition_graph(n, rp, col, prm.slice_rows, part, prm.threads);
   }
   P.nparts = nparts;
   const double t1 = now_ms();

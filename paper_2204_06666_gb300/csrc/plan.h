@@ -72,6 +72,9 @@ int32_t eq1_slice_rows(int64_t n, int tau, int P, int64_t budget_bytes);
 int32_t partition_graph(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t cap,
                         std::vector<int32_t>& part, int threads = 0);
 
+// above this many parts the planner uses greedy growing even when the multilevel partitioner is asked for
+constexpr int64_t kMaxMultilevelParts = 16384;
+
 // Partition the same graph by multilevel recursive bisection into ceil(n / cap) parts of at most `cap`
 // vertices each; `seed` fixes the matching order of the coarsening.  Returns the number of parts; the
 // result does not depend on `threads`.

@@ -129,3 +129,13 @@ def test_multilevel_cuts_fewer_entries_than_greedy_growing():
         kw = dict(slice_rows=cap) if cap else dict()
         g, m = _er_fraction(A, **kw), _er_fraction(A, partitioner=1, **kw)
         assert m < g, (A.name, g, m)
+
+
+def test_very_many_parts_fall_back_to_greedy_growing():
+    # 20,000 rows in parts of one row: far more parts than the multilevel scheme is meant for
+    A = gen.random_csr(20000, 8, mean_row=5, empty_frac=0.0)
+    ex = _plan(A, slice_rows=1, partitioner=1).export()
+    assert ef.same_multiset(ef.decode(ex), ef.triplets(A))
+    assert np.all(np.diff(ex["part_ptr"]) == 1)
+    g = _plan(A, slice_rows=1).export()
+    assert np.array_equal(np.asarray(ex["new_to_old"]), np.asarray(g["new_to_old"]))
