@@ -164,12 +164,14 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
 ehyb_status_t ehyb_destroy(ehyb_plan_t plan);
 
 /*
- * y = A x in FP64 (Alg. 3), x and y device arrays of n doubles in the ORIGINAL numbering.
- * Launches: a gather x_p = x[new_to_old] into plan workspace, then one block per partition
- * (stage slice of x_p into shared memory, slab from shared memory, ER lines with global
- * gathers) writing y[new_to_old[r]] directly.  Effective bytes per call (ehyb_plan_info):
- * 10 per slab entry (value + 16-bit column), 12 per ER entry, 8 per ER line (yIdxER and its
- * CSR offset), and 8 n each for x and y.
+ * y = A x in FP64 (Alg. 3, Sec. 3.2), x and y device arrays of n doubles in the ORIGINAL numbering.
+ * With the default sliced ER layout this is ONE launch, one block per partition: the block gathers its
+ * slice of x through new_to_old into shared memory (CachedVec), multiplies the slab from shared memory,
+ * adds the ER entries of the same slices with x read from global memory through columns in the original
+ * numbering, and writes y[new_to_old[r]] directly.  With er_layout 1 a gather kernel first writes
+ * x_p = x[new_to_old] to plan workspace and the ER lines run after the slab.  Effective bytes per call
+ * (ehyb_plan_info): 10 per slab entry (value + 16-bit column), 12 per ER entry, 8 n each for x and y,
+ * plus 8 per ER line (yIdxER and its CSR offset) with er_layout 1.
  */
 ehyb_status_t ehyb_spmv(ehyb_plan_t plan, const double* x, double* y, void* stream);
 
@@ -180,18 +182,20 @@ ehyb_status_t ehyb_spmv_permuted(ehyb_plan_t plan, const double* xp, double* yp,
 ehyb_status_t ehyb_permute(ehyb_plan_t plan, int32_t to_new, const double* in, double* out, void* stream);
 
 /*
- * y = A x with HOST x and y (n doubles each): copies x in, runs ehyb_spmv, copies y out, on
- * `stream`, and waits for the stream.  Pinned host memory makes the copies asynchronous DMA.
+ * y = A x (the product of ehyb_spmv, Alg. 3) with HOST x and y (n doubles each): copies x in, runs
+ * ehyb_spmv, copies y out, on `stream`, and waits for the stream.  Pinned host memory makes the copies
+ * asynchronous DMA.  On an error the stream is drained before the call returns.
  */
 ehyb_status_t ehyb_spmv_host(ehyb_plan_t plan, const double* x_host, double* y_host, void* stream);
 
 /*
- * y_i = A x_i for `count` pairs of HOST vectors (x_host[i], y_host[i]: n doubles each), pipelined: the copy
+ * y_i = A x_i (the product of ehyb_spmv, Alg. 3; the paper's use is many products with one plan, Sec. 6)
+ * for `count` pairs of HOST vectors (x_host[i], y_host[i]: n doubles each), pipelined: the copy
  * of x_{i+1} into the device and the copy of y_{i-1} out of it overlap the product of step i (two device
  * buffer pairs; the copies run on two streams of the plan's own, the products on `stream`).  Every y_i is
  * on the host when the call returns; each equals ehyb_spmv's result bit for bit.  Host memory should be
  * pinned (pageable memory works, without the overlap).  NULL arrays or entries give EHYB_ERR_INVALID_ARG;
- * count 0 does nothing.
+ * count 0 does nothing.  On an error every stream is drained before the call returns.
  */
 ehyb_status_t ehyb_spmv_host_many(ehyb_plan_t plan, int32_t count, const double* const* x_host,
                                   double* const* y_host, void* stream);
