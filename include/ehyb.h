@@ -4,8 +4,9 @@
  *
  * Method (Sec. 3, Sec. 4):
  *   1. The rows of A are partitioned as an undirected graph so that most entries have
- *      row and column in the same partition (Sec. 3.1; graph growing here, METIS in the
- *      paper), with at most VecSize rows per partition chosen by Eq. 1 / Eq. 2 (Sec. 3.3).
+ *      row and column in the same partition (Sec. 3.1; greedy graph growing or a multilevel
+ *      scheme here, METIS in the paper), with at most VecSize rows per partition chosen by
+ *      Eq. 1 / Eq. 2 (Sec. 3.3).
  *   2. Rows are renumbered partition by partition, each partition sorted by its number
  *      of in-partition entries, descending (Alg. 1).
  *   3. In-partition entries go to a sliced ELL slab (32-lane slices stored column-major)
@@ -13,8 +14,9 @@
  *      Alg. 2); the others go to the extra-rows (ER) part, each ER line mapped back to
  *      its row by yIdxER (Sec. 3.2).
  *   4. On the GPU one thread block per partition stages its slice of x into shared memory
- *      with a bulk asynchronous copy, runs the slab from shared memory, then adds the ER
- *      lines of its rows with global gathers (Alg. 3).
+ *      (gathered through the permutation, or with a bulk asynchronous copy in the plan's
+ *      numbering), runs the slab from shared memory, and adds the ER entries of its rows
+ *      with global gathers (Alg. 3).
  *
  * Conventions for every call:
  *   - Every function returns an ehyb_status_t and never aborts the process.
