@@ -11,7 +11,8 @@ struct DevPlan {
   int64_t n = 0;
   int32_t nparts = 0, tpr = 1, er_tpr = 1, threads = 512;
   int32_t max_part_rows = 0;
-  int32_t kbatch = 8;  // slots loaded ahead of their FMAs: 6 for FP64 on wide slices (>= 32 slots a lane), else 8
+  int32_t kbatch = 8;  // FP64 batch depth (two pipelined half-batches): 6 on wide slices (>= 32 slots a lane), else 8;
+                       // the FP32 / BF16 kernels always hold 12
   const int32_t* new_to_old = nullptr;
   const int32_t* part_ptr = nullptr;
   const int32_t* slice_ptr = nullptr;
