@@ -77,6 +77,9 @@ def test_host_only_plan_refuses_device_calls():
     P = eh.Plan(A, host_only=1)
     assert eh._lib.ehyb_spmv(P.handle, None, None, None) == 7
     assert eh._lib.ehyb_plan_check(P.handle) == 7
+    assert eh._lib.ehyb_spmv_host(P.handle, None, None, None) == 7
+    assert eh._lib.ehyb_spmv_host_many(P.handle, 1, None, None, None) == 7
+    assert eh._lib.ehyb_spmv_host_many(None, 0, None, None, None) == 1      # no plan
 
 
 def test_no_device_is_reported_without_gpu():
