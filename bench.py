@@ -1,25 +1,32 @@
 #!/usr/bin/env python3
 """EHYB FP64 SpMV benchmark on GB300.
 
-One step = one y = A x through the C ABI (ehyb_spmv: gather of x into the plan numbering +
-the fused slab/ER kernel writing y in the original numbering) on the 3D Q1 hex elasticity
-matrix (70^3 nodes x 3 dof: n = 1,029,000, nnz = 80,990,208), x ~ U[-1, 1) seeded.
+One step = one y = A x through the C ABI (ehyb_spmv: one fused launch that gathers x through the
+permutation into shared memory, runs the slab and the ER entries and writes y in the original
+numbering) on the 3D Q1 hex elasticity matrix (70^3 nodes x 3 dof: n = 1,029,000,
+nnz = 80,990,208), x ~ U[-1, 1) seeded.
 
 Prints ONE JSON line (rank 0).  value = whole-job GFLOP/s (2 nnz per SpMV, padding excluded)
-timed with CUDA events on the launching stream; the matrix (0.85 GB of slab) is larger than
-L2, so every step streams it from HBM.  Also reported:
-  * roofline of the fused kernel: its own CUDA-event time per launch, recorded by the library
-    around every launch in the timed region; algorithmic bytes from the plan (values + 16-bit
-    columns + ER columns + yIdxER/offsets + x + y) and algorithmic FLOPs (2 nnz);
+timed with CUDA events on the launching stream.  A workload larger than L2 (the 3D meshes) runs
+back to back; one that fits L2 (the 2D mesh) is timed cold, a 512 MB write before every step,
+with the warm time in `warm`.  Also reported:
+  * roofline of the fused kernel (achieved / peak, the bound, DRAM traffic from the committed
+    ncu record while the kernel sources and the plan's layout match it);
   * the plain vector-CSR kernel on the same GPU (original and EHYB-reordered row order, best
     lanes-per-row of 1..32);
   * preprocessing (plan build) time as a multiple of one SpMV;
-  * e2e: the same metric through ehyb_spmv_host with pinned host x / y copied every step;
-  * cpu_baseline: the CPU oracle (plain C CSR SpMV, one thread) on a bounded row sample.
+  * e2e: the same metric through the host-vector entries, x copied in and y out every step:
+    ehyb_spmv_host_many (copies overlapping neighbouring products) and, under `sync`, one
+    synchronous ehyb_spmv_host call per step;
+  * cpu_baseline: the CPU oracle (plain C CSR SpMV) on one core over a bounded row sample, and
+    under `multicore` whole products split over every host core.
 
---impl reference times that oracle as the reference arm (there is no runnable reference code).
-Multi-GPU (torchrun): independent replicas, one per rank ("replicas only": the method's kernel
-has no exchange step at one GPU per rank), max time over ranks.
+Other modes: --partitioner 1 (multilevel partition), --lowp (FP32 / BF16 SpMVs), --solver (CG,
+mixed precision, FSAI-PCG to 1e-10), --transient (implicit time steps reusing one plan),
+--batch, --spmm, --plan-io.  --impl reference times the oracle on the host cores as the reference
+arm (there is no runnable reference code).  Multi-GPU (torchrun): independent replicas, one per
+rank ("replicas only": the method's kernel has no exchange step at one GPU per rank), max time
+over ranks.
 """
 from __future__ import annotations
 
