@@ -87,3 +87,13 @@ def test_cpu_baselines_compute_the_product():
     assert one["value"] > 0 and one["cores"] == 1 and one["parity"]["rel_l2"] == 0.0
     multi = one["multicore"]
     assert multi["value"] > 0 and multi["cores"] >= 1 and multi["kind"] == "oracle"
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29563", os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--workload", "fem2d_p1_200", "--steps", "10", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1 and json.loads(lines[0])["impl"] == "reference"
