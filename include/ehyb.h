@@ -30,6 +30,11 @@
  *     (issue them on one stream).  x and y must not alias.
  *   - Device-detected faults (a staging wait that ran out of time) are recorded in a
  *     per-plan status word and returned by the next ehyb_plan_check / ehyb_plan_info.
+ *     After a timed-out wait the block waits up to eight more time limits for the copy it
+ *     issued to land before it leaves.  A copy still outstanding after that means the device
+ *     no longer completes copies: it may yet write into shared memory a later block owns, so
+ *     after EHYB_ERR_TIMEOUT discard every result since the last check and launch nothing
+ *     more on that device.
  *   - Accepted matrices: square, 0 <= n < 2^31 - 1, nnz < 2^63; unsorted columns,
  *     duplicate entries (summed like separate terms) and explicit zeros are kept; empty
  *     rows give y_i = 0; n = 0 is a valid no-op.
@@ -210,8 +215,11 @@ ehyb_status_t ehyb_spmv_host_many(ehyb_plan_t plan, int32_t count, const double*
  * array compiled into the library (present on every GPU that loads it, until exit), so the plan
  * may have at most 2^20 rows (EHYB_ERR_TOO_LARGE otherwise).  The call allocates nothing.  The
  * first call on a device looks the array's device address up once, with that device current;
- * make that first call before any stream capture.  All calls share the array: calls that overlap
- * in time on the GPU (other streams, other threads) race on it; each call rewrites what it reads.
+ * make that first call before any stream capture.  The address is kept for the life of the
+ * process: do not use the library across cudaDeviceReset (which also frees every plan's device
+ * arrays).  All calls share the array: calls that overlap in time on the GPU (other streams,
+ * other threads) race on it; each call rewrites what it reads.  A failed CUDA step returns
+ * EHYB_ERR_CUDA with its text in ehyb_last_cuda_error, like every other entry point.
  */
 ehyb_status_t ehyb_spmv_noalloc(ehyb_plan_t plan, const double* x, double* y, void* stream);
 
@@ -328,8 +336,9 @@ ehyb_status_t ehyb_batch_create(int32_t count, const ehyb_plan_t* plans, ehyb_ba
 
 /*
  * ys[i] = A_i xs[i] for every plan of the batch (device arrays, original numbering), asynchronously on
- * `stream`: one gather launch over all plans and one persistent launch whose blocks pull partitions
- * from a shared queue, both replayed from a CUDA graph captured on the first call.  Results equal
+ * `stream`: ONE persistent launch whose blocks pull (plan, partition) tiles from a shared queue, each
+ * tile gathering its slice of x through its plan's permutation as it stages it, replayed from a CUDA
+ * graph captured on the first call.  Results equal
  * ehyb_spmv on each plan bit for bit.  Uses the plans' workspaces: do not overlap with other calls on
  * the same plans.  xs / ys are host arrays of `count` device pointers.
  */
@@ -386,6 +395,16 @@ ehyb_status_t ehyb_csr_create(int64_t n, int64_t nnz, const int64_t* row_ptr, co
 ehyb_status_t ehyb_csr_spmv(ehyb_csr_t m, const double* x, double* y, void* stream);
 ehyb_status_t ehyb_csr_set_tpr(ehyb_csr_t m, int32_t tpr);
 ehyb_status_t ehyb_csr_destroy(ehyb_csr_t m);
+
+/*
+ * Measure the FP64 FMA throughput of the current device: every thread of a grid of 4 x 512-thread
+ * blocks per SM runs 8 independent chains of `iters` fused multiply-adds; the best of `reps` timed
+ * launches (CUDA events, after one untimed launch) gives *tflops = 2 x FMAs / time and *ms_best.  An FP64
+ * SpMV spends one FMA per stored entry (Alg. 3), so this rate, not HBM, bounds it on a part whose FP64
+ * pipe is narrow; the roofline of the FP64 kernels is taken against it.  Synchronous; allocates and
+ * frees its output array.  iters = 4096 takes about 16 ms per launch on a 152-SM part at 2.07 GHz.
+ */
+ehyb_status_t ehyb_fp64_fma_peak(int32_t iters, int32_t reps, double* tflops, double* ms_best);
 
 /* ---- knob tuning (not in the paper: Eq. 1 fixes VecSize; this chooses VecSize, the slab width cap and
  *      the lanes per row per matrix) ---- */

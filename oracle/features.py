@@ -1,6 +1,7 @@
 """Independent numpy statement of the tuner's 16 matrix features -- TEST INFRASTRUCTURE ONLY.
 
-Written from the feature definitions (not from the library's code) to pin ``ehyb_features``:
+Written from the feature definitions (not from the library's code) to pin ``ehyb_features``; every output is
+pinned to closed forms in tests/test_oracle_features.py:
 0 log2(n+1); 1 log2(nnz+1); 2 mean, 3 population std, 4 log2(max+1), 5 min, 6 p50, 7 p90, 8 p99 of the
 row lengths (percentile q = element floor(q (n-1)) of the ascending lengths); 9 share of rows longer
 than 32; 10 Gini coefficient sum_i (2i - n - 1) l_(i) / (n sum l) over ascending lengths, ranks from 1;

@@ -131,6 +131,7 @@ _sig("ehyb_mlp_workspace_bytes", [_I32], _I64)
 _sig("ehyb_mlp_forward", [_P, _P, _I32, _P, _P, _P])
 _sig("ehyb_mlp_loss_grad", [_P, _P, _P, _I32, _P, _P, _P, _P])
 _sig("ehyb_mlp_adam", [_P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P])
+_sig("ehyb_fp64_fma_peak", [_I32, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)])
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
@@ -246,6 +247,13 @@ def ehyb_plan_save(plan, path: str):
 def ehyb_plan_load(path: str, opt: Options | None, stream, out: ctypes.c_void_p):
     return _lib.ehyb_plan_load(os.fsencode(path), ctypes.byref(opt) if opt is not None else None, stream,
                                ctypes.byref(out))
+
+
+def fp64_fma_peak(iters: int = 8192, reps: int = 5) -> tuple[float, float]:
+    """(TFLOP/s, best launch ms) of the current device's FP64 FMA pipe (ehyb_fp64_fma_peak)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ehyb_fp64_fma_peak(iters, reps, ctypes.byref(tf), ctypes.byref(ms)), "ehyb_fp64_fma_peak")
+    return tf.value, ms.value
 
 
 def ehyb_test_fail_allocs_after(count: int):

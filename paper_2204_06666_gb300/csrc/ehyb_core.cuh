@@ -32,6 +32,7 @@ namespace core {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTimeoutCode = 9;  // EHYB_ERR_TIMEOUT
 constexpr int kBoundsCode = 12;  // EHYB_ERR_BOUNDS
+constexpr int kDrainLimits = 8;  // time limits a timed-out block waits for its own staging copy to land
 
 // Checked build (-DEHYB_BOUNDS_CHECK=1): every index the kernels compute into shared memory, x and y is
 // tested against its buffer; a violation records EHYB_ERR_BOUNDS in the plan status word and the access
@@ -99,6 +100,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
   return true;
+}
+
+// Wait (bounded) for the staging copy counted on `bar`.  On expiry record EHYB_ERR_TIMEOUT and, when the
+// copy was issued, wait up to kDrainLimits more time limits for it to land before the block's shared
+// memory goes away; past that the device no longer completes copies, the block leaves anyway (every wait
+// is bounded) and the status word tells the host to stop using the device.  Returns false on expiry.
+__device__ __forceinline__ bool staging_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns, bool issued,
+                                             int32_t* status) {
+  if (mbar_wait_bounded(bar, parity, limit_ns)) return true;
+  atomicCAS(status, 0, kTimeoutCode);
+  if (issued)
+    for (int r = 0; r < kDrainLimits && !mbar_wait_bounded(bar, parity, limit_ns); ++r) {
+    }
+  return false;
 }
 
 // Programmatic dependent launch: let the next kernel in the stream be scheduled now / wait until the
@@ -324,12 +339,7 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     int ok = 1;
     if (bulk_bytes) {
       const uint32_t par = bs.phase & 1u;
-      ok = mbar_wait_bounded(&bs.bar, par, a.timeout_ns) ? 1 : 0;
-      if (!ok) {
-        atomicCAS(a.status, 0, kTimeoutCode);
-        // a copy that was issued must land before the block's shared memory goes away
-        if (!a.inject) mbar_wait_bounded(&bs.bar, par, a.timeout_ns);
-      }
+      ok = staging_wait(&bs.bar, par, a.timeout_ns, !a.inject, a.status) ? 1 : 0;
       bs.phase += 1;
     }
     bs.stage_ok = ok;

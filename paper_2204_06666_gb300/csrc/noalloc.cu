@@ -28,12 +28,15 @@ static __device__ __align__(256) double g_noalloc_xp[EHYB_NOALLOC_MAX_ROWS];
 namespace ehyb {
 // defined in api.cpp: device view of a plan (nullptr for host-only plans)
 const DevPlan* plan_device_view(ehyb_plan_t plan, int* device);
+// records the CUDA error text for ehyb_last_cuda_error and returns EHYB_ERR_CUDA
+ehyb_status_t cuda_error_status(cudaError_t e, const char* what);
 }  // namespace ehyb
 
 namespace {
 
 // Device address of g_noalloc_xp, looked up once per device (the name itself is only a host-side
-// stand-in in host code).  The lookup happens on the first call made with that device current.
+// stand-in in host code).  The lookup happens on the first call made with that device current and is
+// kept for the life of the process (a cudaDeviceReset would invalidate it, as it frees every plan).
 double* scratch_address(int dev, cudaError_t* err) {
   static std::mutex mu;
   static double* addr[128] = {nullptr};
@@ -66,13 +69,15 @@ extern "C" ehyb_status_t ehyb_spmv_noalloc(ehyb_plan_t plan, const double* x, do
   if (D->n == 0) return EHYB_OK;
   if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return EHYB_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ehyb::cuda_error_status(e, "ehyb_spmv_noalloc: cudaGetDevice");
   if (dev != plan_dev) return EHYB_ERR_INVALID_ARG;  // the plan's arrays live on another device
-  cudaError_t e;
   double* xp = scratch_address(dev, &e);
-  if (!xp) return EHYB_ERR_CUDA;
+  if (!xp) return ehyb::cuda_error_status(e, "ehyb_spmv_noalloc: cudaGetSymbolAddress");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (ehyb::launch_permute_f64(*D, 1, x, xp, s) != cudaSuccess) return EHYB_ERR_CUDA;
-  if (ehyb::launch_ehyb_f64(*D, xp, y, 1, s) != cudaSuccess) return EHYB_ERR_CUDA;
+  if ((e = ehyb::launch_permute_f64(*D, 1, x, xp, s)) != cudaSuccess)
+    return ehyb::cuda_error_status(e, "ehyb_spmv_noalloc: permute launch");
+  if ((e = ehyb::launch_ehyb_f64(*D, xp, y, 1, s)) != cudaSuccess)
+    return ehyb::cuda_error_status(e, "ehyb_spmv_noalloc: product launch");
   return EHYB_OK;
 }

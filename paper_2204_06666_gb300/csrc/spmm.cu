@@ -64,11 +64,7 @@ __global__ void __launch_bounds__(512) spmm_kernel(KArgs a, const double* __rest
   if (tid == 0) {
     int ok = 1;
     if (bulk_bytes) {
-      ok = mbar_wait_bounded(&bs.bar, 0, a.timeout_ns) ? 1 : 0;
-      if (!ok) {
-        atomicCAS(a.status, 0, kTimeoutCode);
-        if (!a.inject) mbar_wait_bounded(&bs.bar, 0, a.timeout_ns);
-      }
+      ok = staging_wait(&bs.bar, 0, a.timeout_ns, !a.inject, a.status) ? 1 : 0;
     }
     bs.stage_ok = ok;
   }

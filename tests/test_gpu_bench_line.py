@@ -21,17 +21,21 @@ def _line(*args):
 
 
 def test_default_workload_line_keeps_the_contract():
-    d = _line("--steps", "200", "--warmup", "3", "--skip-csr", "--cpu-seconds", "1")
+    d = _line("--steps", "20", "--warmup", "3", "--skip-csr", "--cpu-seconds", "1")
     for k, t in (("metric", str), ("value", float), ("unit", str), ("n_gpus", int), ("steps", int),
                  ("warmup", int), ("ms_per_step", float), ("higher_is_better", bool), ("scaling", str),
                  ("dtype", str), ("data", str), ("config", dict), ("roofline", dict), ("e2e", dict),
                  ("gpu_launches", int), ("clocks", dict), ("cpu_baseline", dict)):
         assert isinstance(d[k], t), k
-    assert d["vs_baseline"] is None and d["n_gpus"] == 1 and d["steps"] == 200 and d["dtype"] == "f64"
+    assert d["vs_baseline"] is None and d["n_gpus"] == 1 and d["steps"] == 20 and d["dtype"] == "f64"
     assert d["config"]["workload"] == "hex_elast3d_70" and d["value"] > 0
     r = d["roofline"]
     assert r["bound"] in ("alu", "hbm") and 0 < r["frac"] < 1.2 and r["peak"] > 0 and r["unit"] in ("TFLOP/s", "GB/s")
     assert abs(r["achieved"] / r["peak"] - r["frac"]) < 1e-9
+    fp64 = r if r["bound"] == "alu" else r["alu"]
+    assert fp64["peak_source"].startswith("measured") and 0.3 < fp64["peak"] / fp64["peak_nominal"] < 1.1
+    lw = d["long_window"]                   # a 20-step window is repeated over 2000 steps beside it
+    assert lw["steps"] == 2000 and 0.5 < lw["ms_per_step"] / d["ms_per_step"] < 2.0
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 8 * d["config"]["n"]
     assert e["bit_identical_to_device_entry"] and e["sync"]["value"] > 0
@@ -47,3 +51,14 @@ def test_l2_resident_workload_is_timed_cold():
     assert "flushes L2" in d["config"]["l2"]
     assert d["warm"]["ms_per_step"] > 0 and d["warm"]["value"] > 0
     assert d["ms_per_step"] >= 0.8 * d["warm"]["ms_per_step"]     # a flushed step is not faster than a warm one
+
+
+def test_fp64_probe_measures_a_plausible_rate():
+    import torch
+    import paper_2204_06666_gb300 as eh
+    torch.cuda.set_device(0)
+    tf, ms = eh.fp64_fma_peak(iters=1024, reps=3)
+    nominal = 2 * 2 * torch.cuda.get_device_properties(0).multi_processor_count * 2.07e9 / 1e12
+    assert ms > 0 and 0.3 * nominal < tf < 1.1 * nominal     # at most the nominal rate, well above a stall
+    with pytest.raises(eh.EhybError):
+        eh.fp64_fma_peak(iters=0)

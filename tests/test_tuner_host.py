@@ -9,10 +9,24 @@ from oracle import ehyb_format as ef
 from oracle import features as of
 
 
+def _pinned(name):
+    # matrices whose oracle features are pinned to closed forms in test_oracle_features.py
+    n = 300
+    if name == "lower_triangle":
+        rows = [np.arange(i + 1) for i in range(n)]
+    else:
+        rows = [np.array([n - 1 - i]) for i in range(n)]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    return gen.CSR(n, rp, col, np.ones(col.size))
+
+
 @pytest.mark.parametrize("make", [lambda: gen.fem2d_p1(N=40), lambda: gen.hex_elast3d(N=6),
                                   lambda: gen.random_csr(900, 3, mean_row=7, long_rows=4, long_len=300,
                                                          empty_frac=0.05, symmetric=True),
-                                  lambda: gen.random_csr(500, 4, mean_row=12, duplicates=True)])
+                                  lambda: gen.random_csr(500, 4, mean_row=12, duplicates=True),
+                                  lambda: _pinned("lower_triangle"), lambda: _pinned("anti_diagonal")])
 def test_features_match_independent_statement(make):
     import paper_2204_06666_gb300 as eh
     A = make()
