@@ -604,8 +604,9 @@ def run_transient(args):
 
 
 def run_solver(args):
-    """Time to a 1e-10 relative residual: FP64 CG vs FP64 refinement around FP32 / BF16 inner CG, both as
-    restarted refinement (refine 1 / 2) and as residual replacement that keeps the direction (refine 3 / 4),
+    """Time to a 1e-10 relative residual: FP64 CG vs FP64 refinement around FP32 / BF16 inner CG, as
+    restarted refinement (refine 1 / 2), as residual replacement that keeps the direction (refine 3 / 4) and as
+    flexible FP64 CG with the inner solve as its preconditioner (refine 5 / 6),
     and FSAI-preconditioned CG (G in FP64 / FP32 / BF16; FP64 PCG and FP32 PCG with FP64 residual
     replacement every 10x or 100x).  The line's value is the FP32 PCG with BF16 G and replacement every 100x.
 
@@ -635,7 +636,8 @@ def run_solver(args):
     out = {}
     x_ref = None
     for name, plan, refine in (("fp64_cg", P32, 0), ("refined_fp32", P32, 1), ("refined_bf16", P16, 2),
-                               ("replaced_fp32", P32, 3), ("replaced_bf16", P16, 4)):
+                               ("replaced_fp32", P32, 3), ("replaced_bf16", P16, 4),
+                               ("flexible_fp32", P32, 5), ("flexible_bf16", P16, 6)):
         times, res = [], None
         for rep in range(args.solver_reps + 1):
             x = torch.zeros_like(b)
@@ -652,6 +654,7 @@ def run_solver(args):
             x_ref = xh
         out[name] = {"status": eh.STATUS.get(st, st), "converged": bool(info["converged"]),
                      "iterations": info["iterations"], "refinements": info["refinements"],
+                     "flexible": bool(info["flexible"]),
                      "seconds": statistics.median(times), "relres_fp64": info["relres"],
                      "err_vs_xstar": float(np.linalg.norm(xh - xstar) / np.linalg.norm(xstar)),
                      "err_vs_fp64_cg": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)),

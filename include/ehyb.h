@@ -102,6 +102,10 @@ typedef struct {
                                 size; more than 16,384 parts fall back to greedy growing); other values give
                                 EHYB_ERR_INVALID_ARG.  The exhaustive sweep (tuner 2) times greedy-growing
                                 partitions only */
+  int32_t lowp_group;        /* slot layout of the lowp value copies: 1 = column-major like the FP64 arrays,
+                                4 = each lane's slots in runs of four (one vector load per run; the copies get
+                                their own column arrays in that layout), 0 = 4 when a slice holds 32 or more
+                                slab + sliced-ER slots per lane on average, else 1.  Results do not depend on it. */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;
@@ -124,6 +128,8 @@ typedef struct {
   int32_t tuner_path;        /* 0 options as given, 1 learned choice kept, 2 sweep, 3 learned choice failed its
                                 sanity check and the sweep decided */
   int32_t ell_width_cap;     /* slab width cap in force (0 = none) */
+  int32_t lowp_group;        /* slot layout of the lowp copies in force (1 or 4; see ehyb_options_t) */
+  int32_t pad;
 } ehyb_plan_info_t;
 
 /* Pointers into arrays owned by the plan (valid until ehyb_destroy); see ehyb_plan_export. */
@@ -151,6 +157,14 @@ typedef struct {
   const int32_t* er_scol;        /* [er_stored] (padding: first row of the partition, value 0) */
   const double* er_sval;         /* [er_stored] */
   const int32_t* row_er_count;   /* [n]: extra entries of each new row */
+  /* the lowp value copies (plans that keep host arrays only: host_only or keep_host; NULL otherwise):
+   * FP32 (lowp 1) or BF16 bits (lowp 2) in the slot layout lowp_group (options.lowp_group), with their own
+   * slab / sliced-ER columns when lowp_group is 4 (the FP64 arrays' columns when it is 1) */
+  int32_t lowp, lowp_group;
+  const void* ell_val_low;       /* [ell_stored] */
+  const uint16_t* ell_col_low;   /* [ell_stored] */
+  const void* er_sval_low;       /* [er_stored] */
+  const int32_t* er_scol_low;    /* [er_stored] */
 } ehyb_plan_export_t;
 
 const char* ehyb_status_string(ehyb_status_t s);
@@ -242,7 +256,8 @@ typedef struct {
   int32_t iterations;        /* CG iterations (refinement: inner iterations summed over the outer steps) */
   int32_t refinements;       /* FP64 residual corrections (refine != 0) */
   int32_t converged;         /* 1 when the stopping test was met */
-  int32_t pad;
+  int32_t flexible;          /* 1 when the flexible FP64 CG with the low-precision solve as preconditioner ran
+                                (refine 5 / 6, or taking over a stalled BF16 refinement, refine 2 / 4) */
   double relres;             /* ||b - A x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
   double relres_recursive;   /* FP64 CG: sqrt(r.r)/||b|| of the recursion at exit; refinement: last outer residual */
   double seconds;            /* host wall time of the call */
@@ -264,6 +279,13 @@ typedef struct {
  *               its residual has dropped by the factor inner_rtol (0 = 0.1), x += s d in FP64, the
  *               residual is recomputed in FP64 and the iteration continues on it (direction rescaled,
  *               not restarted).  Stops on the FP64 residual <= rtol ||b|| or max_iter iterations.
+ *   refine = 5 / 6: flexible CG (Notay's FCG keeping one direction) in FP64 whose preconditioner is an
+ *               inner CG on the FP32 (5) / BF16 (6) values (plan with opt.lowp = 1 / 2), from 0 on
+ *               r / ||r||, to the relative residual inner_rtol (0 = 0.1) or 500 iterations; each outer
+ *               step is one FP64 product q = A p with p A-orthogonal to the previous direction.  The FP64
+ *               outer iteration carries the accuracy, so it converges where u_bf16 kappa(A) >= 1 makes
+ *               refine 2 / 4 stall; those two hand a stalled solve over to it (info->flexible = 1).
+ *               iterations counts inner iterations, refinements the outer steps.
  * Requires the sliced ER layout (er_layout 0).  Returns EHYB_ERR_NOT_CONVERGED (info filled) when the
  * test was not met.  The solver workspace (5 FP64 + 4 FP32 vectors) is allocated on the first call.
  */
@@ -272,6 +294,84 @@ ehyb_status_t ehyb_cg(ehyb_plan_t plan, const double* b, double* x, double rtol,
 
 /* r.r of the recursion for iterations 0..count-1 of the last FP64 CG solve (or of the last inner solve). */
 ehyb_status_t ehyb_cg_history(ehyb_plan_t plan, double* hist, int32_t cap, int32_t* count);
+
+/* ---- row shards for several GPUs: the halo-exchange form of the method ---- */
+
+/*
+ * The partitions of a plan are contiguous ranges of the reordered rows, and a partition's slab reads only
+ * its own slice of x (Sec. 3.1-3.2): only the extra-row (ER) entries reach other rows.  A shard is one
+ * rank's contiguous group of partitions (about 1/nranks of the stored slots each).  Its ER columns are
+ * renumbered into x_ext = [x_local | halo]: x_local = the rank's rows [row_begin, row_end) of x in the
+ * plan's numbering, halo = the other ranks' rows its ER entries read (halo_rows, ascending, hence grouped
+ * by owning rank).  One product on every rank is then
+ *     ehyb_shard_pack(x_local -> send_buf);  all-to-all: send_buf -> x_ext + n_local;  ehyb_shard_spmv
+ * where rank r sends send_buf[send_ptr[q] : send_ptr[q+1]] to every q and receives from q into halo
+ * positions [recv_ptr[q], recv_ptr[q+1]) (counts match pairwise by construction).  Every row is summed in
+ * the plan's order, so the shards' y_local concatenated equal ehyb_spmv_permuted's result bit for bit.
+ * The library itself never communicates: the caller moves the halo (NCCL, MPI, peer copies).
+ */
+typedef struct ehyb_shard_s* ehyb_shard_t;
+
+typedef struct {
+  int32_t nranks, rank;
+  int32_t part_begin, part_end;   /* the plan's partitions of this rank */
+  int64_t row_begin, row_end;     /* its rows, plan numbering */
+  int64_t n_local;                /* row_end - row_begin */
+  int64_t n_halo;                 /* remote x entries read by its ER entries */
+  int64_t send_total;             /* entries it sends per exchange (all peers) */
+  int64_t slab_stored, er_stored; /* its slab and sliced-ER slots */
+  int32_t device_status;          /* its device status word (as ehyb_plan_check, not cleared) */
+  int32_t pad;
+} ehyb_shard_info_t;
+
+/*
+ * Shard `rank` of `nranks` of a plan built with the sliced ER layout (EHYB_ERR_UNSUPPORTED otherwise).
+ * Every rank builds the same plan and takes its own shard; the plan may be destroyed afterwards.  A shard
+ * of a host-only plan is host-only (lists and arrays for inspection, no device calls).  Uploads its arrays
+ * to the current device on `stream` and synchronises.  With more ranks than partitions some shards are empty.
+ */
+ehyb_status_t ehyb_shard_create(ehyb_plan_t plan, int32_t nranks, int32_t rank, void* stream, ehyb_shard_t* out);
+ehyb_status_t ehyb_shard_info(ehyb_shard_t shard, ehyb_shard_info_t* info);
+
+/*
+ * Host copies of the exchange lists (each pointer may be NULL): send_ptr, recv_ptr (nranks + 1 each),
+ * send_idx (send_total local rows, grouped by destination rank), halo_rows (n_halo plan rows).
+ */
+ehyb_status_t ehyb_shard_lists(ehyb_shard_t shard, int64_t* send_ptr, int32_t* send_idx, int64_t* recv_ptr,
+                               int32_t* halo_rows);
+
+/* The shard's arrays (host copies, valid until ehyb_shard_destroy) in the layout of ehyb_plan_export: n =
+ * n_local, ER columns index x_ext, new_to_old = the original row of each local row. */
+ehyb_status_t ehyb_shard_export(ehyb_shard_t shard, ehyb_plan_export_t* ex);
+
+/* send_buf[i] = x_local[send_idx[i]] (device arrays), asynchronous on `stream`. */
+ehyb_status_t ehyb_shard_pack(ehyb_shard_t shard, const double* x_local, double* send_buf, void* stream);
+
+/* y_local = A_shard x_ext (device arrays: x_ext of n_local + n_halo, y_local of n_local), asynchronous. */
+ehyb_status_t ehyb_shard_spmv(ehyb_shard_t shard, const double* x_ext, double* y_local, void* stream);
+
+/*
+ * The caller's communication for ehyb_shard_cg; each returns 0 on success.  exchange: called with `stream`
+ * idle and send_dev (the caller's send_buf) packed; must leave the halo in halo_dev (p_ext + n_local, n_halo
+ * doubles on the device) before it returns.  allreduce: sums `count` host doubles over all ranks in place;
+ * every rank must get the same sums.
+ */
+typedef int32_t (*ehyb_exchange_fn)(void* ctx, const double* send_dev, double* halo_dev, void* stream);
+typedef int32_t (*ehyb_allreduce_fn)(void* ctx, double* values, int32_t count);
+
+/*
+ * FP64 CG (Hestenes-Stiefel, the solver Sec. 6 motivates) over the shards of all ranks, called by every rank
+ * with its rows of b and x (device, plan numbering; x = initial guess in, solution out) and two device
+ * buffers of the caller's: p_ext (n_local + n_halo doubles: the direction and its halo) and send_buf
+ * (send_total doubles).  Per iteration: one halo exchange of the direction and two scalar sums over ranks
+ * (p.q, then r.r); every rank takes the same decisions from the same sums.  Stops when ||r|| <= rtol ||b||
+ * or after max_iter iterations; info as for ehyb_cg (relres recomputed after the loop).  Synchronous;
+ * allocates its r and q workspace on the first call.
+ */
+ehyb_status_t ehyb_shard_cg(ehyb_shard_t shard, const double* b, double* x, double* p_ext, double* send_buf,
+                            double rtol, int32_t max_iter, ehyb_exchange_fn exchange, ehyb_allreduce_fn allreduce,
+                            void* ctx, ehyb_cg_info_t* info, void* stream);
+ehyb_status_t ehyb_shard_destroy(ehyb_shard_t shard);
 
 /* ---- preconditioned CG (the solver of Sec. 6 with its preconditioner as further EHYB products) ---- */
 

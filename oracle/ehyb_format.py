@@ -5,10 +5,12 @@ the paper's definitions, what they must mean:
 
 * ``decode`` rebuilds the (row, col, val) triplets of A in the ORIGINAL index
   space from the sliced-ELL part (Sec. 3.2, Alg. 2: entries whose row and column
-  lie in the same partition, 32-lane slices stored column-major, 16-bit column
-  offsets into the partition's cached slice of x, Sec. 3.4) and from the extra-rows
-  (ER) part (entries outside the partition, each ER line mapped back to its row by
-  yIdxER, Sec. 3.2).  Every stored entry must come back exactly once.
+  lie in the same partition, 32-lane slices, 16-bit column offsets into the
+  partition's cached slice of x, Sec. 3.4) and from the extra-rows (ER) part
+  (entries outside the partition, each ER line mapped back to its row by yIdxER,
+  Sec. 3.2).  Every stored entry must come back exactly once.
+* ``slot_index`` states where slot k of a lane sits in a slice (the library's slot
+  layout, see below).
 * ``eq1`` is the cache-size rule of Eq. 1 and Eq. 2 (Sec. 3.3).
 * ``ell_bytes_per_entry`` is the Sec. 3.4 footprint model (value + column index).
 
@@ -40,8 +42,41 @@ def ell_bytes_per_entry(tau: int, index_bytes: int) -> int:
     return tau + index_bytes
 
 
-def decode(ex: dict):
-    """Triplets (rows, cols, vals) in the original numbering, ELL entries first then ER.
+GROUP = 4   # slots of one lane kept together in the runs layout of the low-precision copies
+
+
+def slot_index(base: int, width: int, k: int, lane: int, group: int = 1) -> int:
+    """Storage index of slot k (0 <= k < width) of lane `lane` in a 32-lane slice of `width` slots per lane that
+    starts at `base`.  Alg. 2 stores slot k of every lane side by side (column-major: base + 32 k + lane); that
+    is group 1, the layout of the FP64 arrays.  In group 4 (the library's FP32 / BF16 copies of plans with wide
+    slices) only the last width mod 4 slots keep that order; before them, each lane's slots come in runs of 4
+    consecutive slots (one vector load), the 32 lanes' runs for slots 4q..4q+3 side by side:
+    base + 128 q + 4 lane + (k - 4 q).  Either way [base, base + 32 width) is filled exactly once."""
+    grouped = width - width % GROUP if group == GROUP else 0
+    if k < grouped:
+        q, r = divmod(k, GROUP)
+        return base + 32 * GROUP * q + GROUP * lane + r
+    return base + 32 * k + lane
+
+
+def low_values(ex: dict) -> dict:
+    """The exported plan with its low-precision copy in place of the FP64 arrays (values widened to FP64,
+    BF16 bits as the FP32 value with those upper 16 bits), for decode(..., group=ex["lowp_group"])."""
+    q = dict(ex)
+
+    def wide(v):
+        v = np.asarray(v)
+        if v.dtype == np.uint16:
+            v = (v.astype(np.uint32) << 16).view(np.float32)
+        return v.astype(np.float64)
+    q["ell_val"], q["ell_col"] = wide(ex["ell_val_low"]), np.asarray(ex["ell_col_low"], np.uint16)
+    q["er_sval"], q["er_scol"] = wide(ex["er_sval_low"]), np.asarray(ex["er_scol_low"])
+    return q
+
+
+def decode(ex: dict, group: int = 1):
+    """Triplets (rows, cols, vals) in the original numbering, ELL entries first then ER; `group` is the slot
+    layout of the arrays (slot_index).
 
     ``ex`` holds the exported plan arrays: n, tpr (lanes per row in a slice), new_to_old,
     part_ptr, slice_ptr, slice_pos, ell_col (uint16), ell_val, row_ell_count (per new row), and the
@@ -75,7 +110,7 @@ def decode(ex: dict):
                     j = k * tpr + sub          # entry j of this row's ELL entries
                     if j >= cnt[row]:
                         continue
-                    e = pos + 32 * k + lane
+                    e = slot_index(pos, width, k, lane, group)
                     local = int(ell_col[e])
                     assert pb + local < pe, "ELL column outside its partition"
                     rows.append(n2o[row])
@@ -99,7 +134,7 @@ def decode(ex: dict):
                         j = k * tpr + lane % tpr
                         if j >= ecnt[row]:
                             continue
-                        e = er_pos[s] + 32 * k + lane
+                        e = slot_index(er_pos[s], width, k, lane, group)
                         rows.append(n2o[row])
                         cols.append(n2o[er_col[e]])
                         vals.append(er_val[e])

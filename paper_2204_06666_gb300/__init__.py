@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
                 ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32), ("tuner", ctypes.c_int32),
-                ("host_threads", ctypes.c_int32), ("partitioner", ctypes.c_int32)]
+                ("host_threads", ctypes.c_int32), ("partitioner", ctypes.c_int32), ("lowp_group", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -58,7 +58,7 @@ class PlanInfo(ctypes.Structure):
                 ("bytes_device", ctypes.c_int64), ("partition_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
                 ("upload_ms", ctypes.c_double), ("device_status", ctypes.c_int32), ("num_sms", ctypes.c_int32),
                 ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64), ("tuner_path", ctypes.c_int32),
-                ("ell_width_cap", ctypes.c_int32)]
+                ("ell_width_cap", ctypes.c_int32), ("lowp_group", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,16 +71,18 @@ class PlanExport(ctypes.Structure):
                     "new_to_old", "part_ptr", "slice_ptr", "slice_pos", "ell_col", "ell_val", "row_ell_count",
                     "er_part_ptr", "er_row", "er_ptr", "er_col", "er_val")] + [
                 ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64), ("er_slice_pos", ctypes.c_void_p),
-                ("er_scol", ctypes.c_void_p), ("er_sval", ctypes.c_void_p), ("row_er_count", ctypes.c_void_p)]
+                ("er_scol", ctypes.c_void_p), ("er_sval", ctypes.c_void_p), ("row_er_count", ctypes.c_void_p),
+                ("lowp", ctypes.c_int32), ("lowp_group", ctypes.c_int32), ("ell_val_low", ctypes.c_void_p),
+                ("ell_col_low", ctypes.c_void_p), ("er_sval_low", ctypes.c_void_p), ("er_scol_low", ctypes.c_void_p)]
 
 
 class CgInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double),
+                ("flexible", ctypes.c_int32), ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class TuneEntry(ctypes.Structure):
@@ -132,6 +134,29 @@ _sig("ehyb_mlp_forward", [_P, _P, _I32, _P, _P, _P])
 _sig("ehyb_mlp_loss_grad", [_P, _P, _P, _I32, _P, _P, _P, _P])
 _sig("ehyb_mlp_adam", [_P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P])
 _sig("ehyb_fp64_fma_peak", [_I32, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)])
+
+
+class ShardInfo(ctypes.Structure):
+    _fields_ = [("nranks", ctypes.c_int32), ("rank", ctypes.c_int32), ("part_begin", ctypes.c_int32),
+                ("part_end", ctypes.c_int32), ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
+                ("n_local", ctypes.c_int64), ("n_halo", ctypes.c_int64), ("send_total", ctypes.c_int64),
+                ("slab_stored", ctypes.c_int64), ("er_stored", ctypes.c_int64), ("device_status", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32)
+_sig("ehyb_shard_create", [_P, _I32, _I32, _P, ctypes.POINTER(_P)])
+_sig("ehyb_shard_info", [_P, ctypes.POINTER(ShardInfo)])
+_sig("ehyb_shard_lists", [_P, _P, _P, _P, _P])
+_sig("ehyb_shard_export", [_P, ctypes.POINTER(PlanExport)])
+_sig("ehyb_shard_pack", [_P, _P, _P, _P])
+_sig("ehyb_shard_spmv", [_P, _P, _P, _P])
+_sig("ehyb_shard_cg", [_P, _P, _P, _P, _P, _D, _I32, EXCHANGE_FN, ALLREDUCE_FN, _P, ctypes.POINTER(CgInfo), _P])
+_sig("ehyb_shard_destroy", [_P])
 _sig("ehyb_plan_info", [_P, ctypes.POINTER(PlanInfo)])
 _sig("ehyb_plan_check", [_P])
 _sig("ehyb_plan_export", [_P, ctypes.POINTER(PlanExport)])
@@ -403,28 +428,7 @@ class Plan:
     def export(self) -> dict:
         ex = PlanExport()
         _check(_lib.ehyb_plan_export(self._h, ctypes.byref(ex)), "ehyb_plan_export")
-        n, nparts, ns = ex.n, ex.nparts, ex.nslices
-
-        def arr(ptr, count, dt):
-            if count == 0 or not ptr:
-                return np.zeros(count, dt)
-            return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt))),
-                                         (count,)).copy()
-
-        return {"n": n, "tpr": ex.tpr, "nparts": nparts,
-                "new_to_old": arr(ex.new_to_old, n, np.int32), "part_ptr": arr(ex.part_ptr, nparts + 1, np.int32),
-                "slice_ptr": arr(ex.slice_ptr, nparts + 1, np.int32),
-                "slice_pos": arr(ex.slice_pos, ns + 1, np.int64),
-                "ell_col": arr(ex.ell_col, ex.ell_stored, np.uint16),
-                "ell_val": arr(ex.ell_val, ex.ell_stored, np.float64),
-                "row_ell_count": arr(ex.row_ell_count, n, np.int32),
-                "er_part_ptr": arr(ex.er_part_ptr, nparts + 1, np.int32),
-                "er_row": arr(ex.er_row, ex.er_rows, np.int32), "er_ptr": arr(ex.er_ptr, ex.er_rows + 1, np.int64),
-                "er_col": arr(ex.er_col, ex.er_nnz, np.int32), "er_val": arr(ex.er_val, ex.er_nnz, np.float64),
-                "er_layout": ex.er_layout, "er_slice_pos": arr(ex.er_slice_pos, ns + 1, np.int64),
-                "er_scol": arr(ex.er_scol, ex.er_stored if ex.er_layout == 0 else 0, np.int32),
-                "er_sval": arr(ex.er_sval, ex.er_stored if ex.er_layout == 0 else 0, np.float64),
-                "row_er_count": arr(ex.row_er_count, n, np.int32)}
+        return _export_dict(ex)
 
     def profile_enable(self, on: bool = True):
         _check(_lib.ehyb_profile_enable(self._h, int(on)), "ehyb_profile_enable")
@@ -433,6 +437,163 @@ class Plan:
         ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
         _check(_lib.ehyb_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)), "ehyb_profile_read")
         return ms.value, cnt.value
+
+
+def _arr(ptr, count, dt):
+    if count == 0 or not ptr:
+        return np.zeros(count, dt)
+    return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt))), (count,)).copy()
+
+
+def _export_dict(ex: PlanExport) -> dict:
+    n, nparts, ns = ex.n, ex.nparts, ex.nslices
+    arr = _arr
+    low = 1 if (ex.lowp and ex.ell_val_low) else 0   # the lowp copies are exported by host-kept plans only
+    return {"n": n, "tpr": ex.tpr, "nparts": nparts,
+            "new_to_old": arr(ex.new_to_old, n, np.int32), "part_ptr": arr(ex.part_ptr, nparts + 1, np.int32),
+            "slice_ptr": arr(ex.slice_ptr, nparts + 1, np.int32),
+            "slice_pos": arr(ex.slice_pos, ns + 1, np.int64),
+            "ell_col": arr(ex.ell_col, ex.ell_stored, np.uint16),
+            "ell_val": arr(ex.ell_val, ex.ell_stored, np.float64),
+            "row_ell_count": arr(ex.row_ell_count, n, np.int32),
+            "er_part_ptr": arr(ex.er_part_ptr, nparts + 1, np.int32),
+            "er_row": arr(ex.er_row, ex.er_rows, np.int32), "er_ptr": arr(ex.er_ptr, ex.er_rows + 1, np.int64),
+            "er_col": arr(ex.er_col, ex.er_nnz, np.int32), "er_val": arr(ex.er_val, ex.er_nnz, np.float64),
+            "er_layout": ex.er_layout, "er_slice_pos": arr(ex.er_slice_pos, ns + 1, np.int64),
+            "er_scol": arr(ex.er_scol, ex.er_stored if ex.er_layout == 0 else 0, np.int32),
+            "er_sval": arr(ex.er_sval, ex.er_stored if ex.er_layout == 0 else 0, np.float64),
+            "row_er_count": arr(ex.row_er_count, n, np.int32),
+            "lowp": ex.lowp, "lowp_group": ex.lowp_group,
+            "ell_val_low": arr(ex.ell_val_low, low * ex.ell_stored, np.float32 if ex.lowp == 1 else np.uint16),
+            "ell_col_low": arr(ex.ell_col_low, low * ex.ell_stored, np.uint16),
+            "er_sval_low": arr(ex.er_sval_low, low * (ex.er_stored if ex.er_layout == 0 else 0),
+                               np.float32 if ex.lowp == 1 else np.uint16),
+            "er_scol_low": arr(ex.er_scol_low, low * (ex.er_stored if ex.er_layout == 0 else 0), np.int32)}
+
+
+class Shard:
+    """Rank `rank`'s row shard of `plan` among `nranks` (ehyb_shard_*): its partitions, its halo list and the
+    exchange lists.  Vectors are device float64 tensors in the plan's numbering: x_local / y_local hold the
+    rank's rows, x_ext = [x_local | halo].  Communication is the caller's (see TorchComm)."""
+
+    def __init__(self, plan: "Plan", nranks: int, rank: int, stream=None):
+        self._h = ctypes.c_void_p()
+        import torch
+        # a host-only plan gives a host-only shard, which uploads nothing (no stream needed)
+        st = _stream(stream) if (stream is not None or torch.cuda.is_available()) else None
+        _check(_lib.ehyb_shard_create(plan.handle, int(nranks), int(rank), st, ctypes.byref(self._h)),
+               "ehyb_shard_create")
+        i = self.info()
+        self.nranks, self.rank = nranks, rank
+        self.n_local, self.n_halo, self.send_total = i["n_local"], i["n_halo"], i["send_total"]
+        self.row_begin, self.row_end = i["row_begin"], i["row_end"]
+        L = self.lists()
+        self.send_counts = np.diff(L["send_ptr"]).tolist()
+        self.recv_counts = np.diff(L["recv_ptr"]).tolist()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = ShardInfo()
+        _check(_lib.ehyb_shard_info(self._h, ctypes.byref(inf)), "ehyb_shard_info")
+        return inf.as_dict()
+
+    def lists(self) -> dict:
+        inf = self.info()
+        R = inf["nranks"]
+        sp, rp = np.zeros(R + 1, np.int64), np.zeros(R + 1, np.int64)
+        si, hr = np.zeros(inf["send_total"], np.int32), np.zeros(inf["n_halo"], np.int32)
+        _check(_lib.ehyb_shard_lists(self._h, sp.ctypes.data, si.ctypes.data if si.size else None, rp.ctypes.data,
+                                     hr.ctypes.data if hr.size else None), "ehyb_shard_lists")
+        return {"send_ptr": sp, "send_idx": si, "recv_ptr": rp, "halo_rows": hr}
+
+    def export(self) -> dict:
+        ex = PlanExport()
+        _check(_lib.ehyb_shard_export(self._h, ctypes.byref(ex)), "ehyb_shard_export")
+        return _export_dict(ex)
+
+    def pack(self, x_local, send_buf, stream=None):
+        _check(_lib.ehyb_shard_pack(self._h, _dev(x_local, "float64") if self.n_local else None,
+                                    _dev(send_buf, "float64") if self.send_total else None, _stream(stream)),
+               "ehyb_shard_pack")
+
+    def spmv(self, x_ext, y_local, stream=None):
+        _check(_lib.ehyb_shard_spmv(self._h, _dev(x_ext, "float64"), _dev(y_local, "float64"), _stream(stream)),
+               "ehyb_shard_spmv")
+
+    def cg(self, b_local, x_local, comm, rtol: float = 1e-10, max_iter: int = 10000, stream=None):
+        """Distributed FP64 CG (ehyb_shard_cg), called on every rank with its rows; `comm` supplies
+        exchange(shard, send_buf, p_ext) and allreduce(list of floats) -> list.  Returns (status, info)."""
+        import torch
+        dev = x_local.device
+        p_ext = torch.zeros(self.n_local + self.n_halo, dtype=torch.float64, device=dev)
+        send = torch.zeros(max(self.send_total, 1), dtype=torch.float64, device=dev)
+
+        def _exchange(ctx, send_ptr, halo_ptr, stream_ptr):
+            try:
+                comm.exchange(self, send, p_ext)
+                return 0
+            except Exception:   # noqa: BLE001 -- reported to the library as a failed step
+                import traceback
+                traceback.print_exc()
+                return 1
+
+        def _allreduce(ctx, vals, count):
+            try:
+                out = comm.allreduce([vals[i] for i in range(count)])
+                for i in range(count):
+                    vals[i] = float(out[i])
+                return 0
+            except Exception:   # noqa: BLE001
+                import traceback
+                traceback.print_exc()
+                return 1
+        ex_cb, ar_cb = EXCHANGE_FN(_exchange), ALLREDUCE_FN(_allreduce)
+        info = CgInfo()
+        st = _lib.ehyb_shard_cg(self._h, _dev(b_local, "float64") if self.n_local else None,
+                                _dev(x_local, "float64") if self.n_local else None, p_ext.data_ptr(), send.data_ptr(),
+                                float(rtol), int(max_iter), ex_cb, ar_cb, None, ctypes.byref(info), _stream(stream))
+        if st not in (0, EHYB_ERR_NOT_CONVERGED):
+            raise EhybError(st, "ehyb_shard_cg")
+        return st, info.as_dict()
+
+    def close(self):
+        if self._h:
+            _lib.ehyb_shard_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class TorchComm:
+    """The two communication steps of the shard path on torch.distributed (NCCL for device tensors, gloo for
+    host tensors): the halo exchange as one all_to_all_single with the shard's per-peer counts, and the sum of
+    a few scalars as one all_reduce."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist, self.group = dist, group
+
+    def exchange(self, shard: "Shard", send_buf, x_ext):
+        import torch
+        halo = x_ext[shard.n_local:shard.n_local + shard.n_halo]
+        self.dist.all_to_all_single(halo, send_buf[:shard.send_total], output_split_sizes=shard.recv_counts,
+                                    input_split_sizes=shard.send_counts, group=self.group)
+        if halo.is_cuda:
+            torch.cuda.synchronize()
+
+    def allreduce(self, values):
+        import torch
+        dev = "cuda" if self.dist.get_backend(self.group) == "nccl" else "cpu"
+        t = torch.tensor(values, dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, group=self.group)
+        return t.cpu().tolist()
 
 
 class Fsai:

@@ -197,6 +197,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   if (opt.block_threads != 0 && (opt.block_threads < 32 || opt.block_threads > 1024 || opt.block_threads % 32))
     return EHYB_ERR_INVALID_ARG;
   if (opt.er_layout < 0 || opt.er_layout > 1) return EHYB_ERR_INVALID_ARG;
+  if (opt.lowp_group != 0 && opt.lowp_group != 1 && opt.lowp_group != 4) return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
       opt.part_nnz < 0 || opt.host_threads < 0 || opt.partitioner < 0 || opt.partitioner > 1 ||
       opt.num_sms < 0 || opt.wait_timeout_ns < 0)
@@ -268,6 +269,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   prm.ell_width_cap = opt.ell_width_cap;
   prm.ell_tpr = opt.ell_tpr;
   prm.lowp = opt.lowp;
+  prm.lowp_group = opt.lowp_group;
   prm.er_layout = opt.er_layout;
   prm.part_vec = opt.part_vec;
   prm.threads = opt.host_threads;
@@ -353,9 +355,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
   D.er_layout = H.er_layout;
   D.max_part_rows = H.max_part_rows;
   {  // batch depth: mean slab + sliced-ER slots per lane of a slice (measured: 6 is faster from about 32 up)
-    const double slots = (double)(H.slice_pos.empty() ? 0 : H.slice_pos.back()) +
-                         (double)(H.er_slice_pos.empty() ? 0 : H.er_slice_pos.back());
-    const double w = H.nslices ? slots / (32.0 * (double)H.nslices) : 0.0;
+    const double w = mean_slice_width(H);
     D.kbatch = (H.er_layout == 0 && w >= 32.0) ? 6 : 8;
   }
   D.wait_timeout_ns = opt.wait_timeout_ns > 0 ? (uint64_t)opt.wait_timeout_ns : 1000000000ull;
@@ -388,6 +388,9 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     const size_t o_esv = A.add<double>(H.er_sval.size());
     const size_t o_esv32 = A.add<float>(H.er_sval_f32.size());
     const size_t o_esv16 = A.add<uint16_t>(H.er_sval_bf16.size());
+    const size_t o_ecl = A.add<uint16_t>(H.ell_col_low.size());
+    const size_t o_escl = A.add<int32_t>(H.er_scol_low.size());
+    const size_t o_esol = A.add<int32_t>(H.er_scol_old_low.size());
     const size_t o_xp = A.add<double>((size_t)n + 2);
     const size_t o_xp32 = A.add<float>((size_t)n + 4);
     const size_t o_st = A.add<int32_t>(4);
@@ -406,7 +409,8 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     UP(o_ev, H.ell_val) UP(o_ev32, H.ell_val_f32) UP(o_ev16, H.ell_val_bf16) UP(o_epp, H.er_part_ptr)
     UP(o_er, H.er_row) UP(o_erp, H.er_ptr) UP(o_erc, H.er_col) UP(o_erv, H.er_val) UP(o_erv32, H.er_val_f32)
     UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_so, H.slice_order) UP(o_esc, H.er_scol) UP(o_eso, H.er_scol_old) UP(o_esv, H.er_sval)
-    UP(o_esv32, H.er_sval_f32) UP(o_esv16, H.er_sval_bf16)
+    UP(o_esv32, H.er_sval_f32) UP(o_esv16, H.er_sval_bf16) UP(o_ecl, H.ell_col_low) UP(o_escl, H.er_scol_low)
+    UP(o_esol, H.er_scol_old_low)
 #undef UP
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_st, 0, 16, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_xp, 0, ((size_t)n + 2) * 8, s);
@@ -439,6 +443,10 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     D.er_sval_f32 = (const float*)(base + o_esv32);
     D.er_sval_bf16 = (const uint16_t*)(base + o_esv16);
     D.status = (int32_t*)(base + o_st);
+    D.lowp_group = H.lowp_group;
+    D.ell_col_low = H.lowp_group == 1 ? D.ell_col : (const uint16_t*)(base + o_ecl);
+    D.er_scol_low = H.lowp_group == 1 ? D.er_scol : (const int32_t*)(base + o_escl);
+    D.er_scol_old_low = H.lowp_group == 1 ? D.er_scol_old : (const int32_t*)(base + o_esol);
     P->xp = (double*)(base + o_xp);
     P->xp32 = (float*)(base + o_xp32);
     P->upload_ms = now_ms() - t0;
@@ -459,6 +467,9 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     std::vector<double>().swap(h.er_sval);
     std::vector<float>().swap(h.er_sval_f32);
     std::vector<uint16_t>().swap(h.er_sval_bf16);
+    std::vector<uint16_t>().swap(h.ell_col_low);
+    std::vector<int32_t>().swap(h.er_scol_low);
+    std::vector<int32_t>().swap(h.er_scol_old_low);
     std::vector<int32_t>().swap(h.old_to_new);
   }
   *out = P.release();
@@ -685,6 +696,7 @@ ehyb_status_t ehyb_plan_info(ehyb_plan_t p, ehyb_plan_info_t* info) {
   info->er_stored = p->er_stored;
   info->tuner_path = p->tuner_path;
   info->ell_width_cap = p->ell_width_cap;
+  info->lowp_group = H.lowp_group;
   info->bytes_device = (int64_t)p->arena_bytes;
   info->partition_ms = H.partition_ms;
   info->reorder_ms = H.reorder_ms;
@@ -755,6 +767,15 @@ ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
   ex->er_scol = H.er_scol.data();
   ex->er_sval = H.er_sval.data();
   ex->row_er_count = H.row_er_count.data();
+  ex->lowp = p->lowp;
+  ex->lowp_group = H.lowp_group;
+  if (p->host_kept && p->lowp) {
+    const bool g1 = H.lowp_group == 1;
+    ex->ell_val_low = p->lowp == 1 ? (const void*)H.ell_val_f32.data() : (const void*)H.ell_val_bf16.data();
+    ex->er_sval_low = p->lowp == 1 ? (const void*)H.er_sval_f32.data() : (const void*)H.er_sval_bf16.data();
+    ex->ell_col_low = g1 ? H.ell_col.data() : H.ell_col_low.data();
+    ex->er_scol_low = g1 ? H.er_scol.data() : H.er_scol_low.data();
+  }
   return EHYB_OK;
 }
 

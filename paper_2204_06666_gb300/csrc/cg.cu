@@ -34,6 +34,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kVB = 608;  // vector-kernel blocks (4 per SM; 8 per SM measured slower)
 constexpr int kVT = 256;
 constexpr int kChunk = 16;
+constexpr double kFcgInnerRtol = 0.1;  // default inner tolerance of the flexible CG's preconditioning solve
 
 }  // namespace
 
@@ -305,6 +306,49 @@ __global__ void replace_finish_kernel(const double* part_a, int na, double delta
   }
 }
 
+// ---- flexible CG (Notay's FCG with one kept direction), FP64 outer, low-precision inner CG as the variable
+// preconditioner z = B_k(r)
+
+// z = r (use_r: the inner solve gave nothing) or z = scale * d (FP32 -> FP64); partials of z.q
+__global__ void fcg_z_kernel(int64_t n, int use_r, const double* __restrict__ r, const float* __restrict__ d,
+                             double scale, double* __restrict__ z, const double* __restrict__ q, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const double zi = use_r ? r[i] : scale * (double)d[i];
+    z[i] = zi;
+    acc = fma(zi, q[i], acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// p = z + beta p; partials of p.r
+__global__ void fcg_dir_kernel(int64_t n, const double* __restrict__ z, double beta, double* __restrict__ p,
+                               const double* __restrict__ r, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const double pi = fma(beta, p[i], z[i]);
+    p[i] = pi;
+    acc = fma(pi, r[i], acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha q; partials of r.r
+__global__ void fcg_update_kernel(int64_t n, double alpha, const double* __restrict__ p, const double* __restrict__ q,
+                                  double* __restrict__ x, double* __restrict__ r, double* part) {
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -426,9 +470,83 @@ ehyb_status_t sum_parts(CgWork* w, cudaStream_t s, double* out) {
   return EHYB_OK;
 }
 
+ehyb_status_t cg_loop(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s, int* iters, int* converged,
+                      int* breakdown);
+
+// Flexible CG (Notay, "Flexible conjugate gradients", SIAM J. Sci. Comput. 22, 2000; truncation to one
+// direction) in FP64 on the plan's FP64 values, from the x_p, r of w (r = b - A x_p, ||r||^2 = rr): each
+// step applies the variable preconditioner z = B_k(r) = ||r|| d, d from an inner CG on the low-precision
+// values (FP32 vectors, stopped at inner_rtol or inner_max iterations), then
+//   p = z + beta p with beta = -(z . q_prev) / (p_prev . q_prev) (A-orthogonal to the previous direction),
+//   q = A p, alpha = (p . r) / (p . q), x += alpha p, r -= alpha q.
+// The recursive residual decides; on its convergence the true FP64 residual is recomputed and, if it is
+// still too large, the iteration restarts from it.  *iters counts inner iterations, *outer the steps.
+ehyb_status_t fcg_solve(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s, double bnorm, double rtol, int max_iter,
+                        double inner_rtol, double& rr, int* iters, int* outer, int* converged, double* rel_out) {
+  const DevPlan& D = P->dev;
+  const int64_t n = D.n;
+  const int inner_max = 500;
+  double* z = w->xs;
+  double pq_prev = 0.0;
+  bool restart = true;
+  ehyb_status_t st;
+  int true_checks = 0;
+  for (;;) {
+    const double rel = std::sqrt(rr) / bnorm;
+    *rel_out = rel;
+    if (rel <= rtol || rr == 0.0) {
+      // confirm on the true residual (the recursive one may have drifted)
+      CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+      residual_kernel<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, w->part_a);
+      if ((st = sum_parts(w, s, &rr)) != EHYB_OK) return st;
+      *rel_out = std::sqrt(rr) / bnorm;
+      if (*rel_out <= rtol || rr == 0.0 || ++true_checks > 3) {
+        *converged = *rel_out <= rtol || rr == 0.0;
+        return EHYB_OK;
+      }
+      restart = true;  // continue from the true residual with a fresh direction
+    }
+    if (*iters >= max_iter || !std::isfinite(rr)) return EHYB_OK;
+    // z = B(r): inner CG on the low-precision values, from 0, on r / ||r||
+    const double rn = std::sqrt(rr);
+    init32_kernel<<<kVB, kVT, 0, s>>>(n, w->r, 1.0 / rn, w->r32, w->p32, w->d32, w->part_a);
+    const int cap = std::min(inner_max, max_iter - *iters);
+    init_finish_kernel<<<1, 32, 0, s>>>(w->part_a, kVB, nullptr, 0, inner_rtol * inner_rtol, 1, cap, w->hist, w->st);
+    CKC(cudaGetLastError());
+    int it_in = 0, conv_in = 0, brk = 0;
+    if ((st = cg_loop(P, w, lowp, s, &it_in, &conv_in, &brk)) != EHYB_OK) return st;
+    *iters += it_in;
+    // a first-iteration breakdown leaves d = 0: take the unpreconditioned step z = r
+    fcg_z_kernel<<<kVB, kVT, 0, s>>>(n, it_in == 0 ? 1 : 0, w->r, w->d32, rn, z, w->q, w->part_a);
+    double zq = 0.0;
+    if ((st = sum_parts(w, s, &zq)) != EHYB_OK) return st;
+    const double beta = (restart || !(pq_prev > 0.0)) ? 0.0 : -zq / pq_prev;
+    fcg_dir_kernel<<<kVB, kVT, 0, s>>>(n, z, beta, w->p, w->r, w->part_a);
+    double pr = 0.0;
+    if ((st = sum_parts(w, s, &pr)) != EHYB_OK) return st;
+    DotOut dot{w->pq_part, &w->st->arrive_dot, &w->st->pq};
+    CKC(cudaMemsetAsync(&w->st->arrive_dot, 0, sizeof(int32_t), s));
+    CKC(launch_ehyb_f64(D, w->p, w->q, 0, s, &dot));
+    double pq = 0.0;
+    CKC(cudaMemcpyAsync(&pq, &w->st->pq, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKC(cudaStreamSynchronize(s));
+    ++*outer;
+    if (!(pq > 0.0)) return EHYB_OK;  // A is not positive definite along p: stop (not converged)
+    if (!(pr > 0.0)) {                 // not a descent direction: restart from z = B(r) alone
+      if (restart) return EHYB_OK;
+      restart = true;
+      continue;
+    }
+    fcg_update_kernel<<<kVB, kVT, 0, s>>>(n, pr / pq, w->p, w->q, w->xp, w->r, w->part_a);
+    if ((st = sum_parts(w, s, &rr)) != EHYB_OK) return st;
+    pq_prev = pq;
+    restart = false;
+  }
+}
+
 // CG loop on the vectors of w (FP64 or inner FP32); returns iterations and convergence
 ehyb_status_t cg_loop(ehyb_plan_t P, CgWork* w, int lowp, cudaStream_t s, int* iters, int* converged,
-                      int* breakdown = nullptr) {
+                      int* breakdown) {
   CgState h;
   for (;;) {
     ehyb_status_t st = run_chunk(P, w, lowp, s);
@@ -453,8 +571,8 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
   if (!P || !info) return EHYB_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));
   if (P->host_only) return EHYB_ERR_UNSUPPORTED;
-  if (refine < 0 || refine > 4 || !(rtol >= 0.0) || max_iter < 0) return EHYB_ERR_INVALID_ARG;
-  const int lowp = refine == 0 ? 0 : (refine == 1 || refine == 3) ? 1 : 2;
+  if (refine < 0 || refine > 6 || !(rtol >= 0.0) || max_iter < 0) return EHYB_ERR_INVALID_ARG;
+  const int lowp = refine == 0 ? 0 : (refine % 2 == 1) ? 1 : 2;
   if (refine && P->lowp != lowp) return EHYB_ERR_UNSUPPORTED;  // the plan lacks that value copy
   if (P->er_layout != 0) return EHYB_ERR_UNSUPPORTED;            // the fused dot needs the sliced ER layout
   const int64_t n = P->dev.n;
@@ -478,12 +596,26 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
   const double bnorm = bb > 0.0 ? std::sqrt(bb) : 1.0;
 
   int converged = 0, iters = 0, outer = 0;
-  if (refine == 0) {
+  // a stalled BF16 refinement (refine 2 / 4) hands its x and FP64 residual (w->r, rr_stall) to the flexible CG
+  bool stalled = false;
+  double rr_stall = 0.0;
+  if (refine >= 5) {
+    CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));
+    residual_kernel<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, w->part_a);
+    double rr = 0.0;
+    if ((st = sum_parts(w, s, &rr)) != EHYB_OK) return st;
+    double rel = 0.0;
+    const double irtol = inner_rtol > 0.0 ? inner_rtol : kFcgInnerRtol;
+    if ((st = fcg_solve(P, w, lowp, s, bnorm, rtol, max_iter, irtol, rr, &iters, &outer, &converged, &rel)) != EHYB_OK)
+      return st;
+    info->relres_recursive = rel;
+    info->flexible = 1;
+  } else if (refine == 0) {
     CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));
     init64_kernel<<<kVB, kVT, 0, s>>>(n, w->bp, w->q, w->r, w->p, w->part_a, w->part_b);
     init_finish_kernel<<<1, 32, 0, s>>>(w->part_a, kVB, w->part_b, kVB, rtol * rtol, 0, max_iter, w->hist, w->st);
     CKC(cudaGetLastError());
-    if ((st = cg_loop(P, w, 0, s, &iters, &converged)) != EHYB_OK) return st;
+    if ((st = cg_loop(P, w, 0, s, &iters, &converged, nullptr)) != EHYB_OK) return st;
     double rr_last = 0.0;
     CKC(cudaMemcpyAsync(&rr_last, w->hist + iters, sizeof(double), cudaMemcpyDeviceToHost, s));
     CKC(cudaStreamSynchronize(s));
@@ -530,6 +662,10 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
         info->relres_recursive = rel;
         if (rel <= rtol) { converged = 1; break; }
         rejections = rejected ? rejections + 1 : 0;
+        if (rejections >= 3 && std::isfinite(rr) && rr > 0.0) {
+          stalled = true;
+          rr_stall = rr;
+        }
         if (iters >= max_iter || rr == 0.0 || !std::isfinite(rr) || rejections >= 3) break;
         const double ns = std::sqrt(rr);
         if (brk || rejected) {
@@ -558,6 +694,10 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
       const double rel = std::sqrt(rr) / bnorm;
       info->relres_recursive = rel;
       if (rel <= rtol) { converged = 1; break; }
+      if (iters < max_iter && std::isfinite(rr) && (outer >= outer_max || (outer > 0 && !(rel < prev)))) {
+        stalled = true;
+        rr_stall = rr;
+      }
       if (outer >= outer_max || iters >= max_iter || (outer > 0 && !(rel < prev))) break;
       prev = rel;
       ++outer;
@@ -567,11 +707,21 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
                                           w->st);
       CKC(cudaGetLastError());
       int it_in = 0, conv_in = 0;
-      if ((st = cg_loop(P, w, lowp, s, &it_in, &conv_in)) != EHYB_OK) return st;
+      if ((st = cg_loop(P, w, lowp, s, &it_in, &conv_in, nullptr)) != EHYB_OK) return st;
       iters += it_in;
       correct_kernel<<<kVB, kVT, 0, s>>>(n, w->xp, w->d32, rnorm);
       CKC(cudaGetLastError());
     }
+  }
+  if (stalled && lowp == 2 && !converged && iters < max_iter) {
+    // BF16 values and u_bf16 kappa(A) near or above 1: the refinement stalls; the flexible CG keeps the
+    // BF16 solve as a preconditioner only and lets the FP64 outer iteration carry the accuracy
+    double rel = 0.0;
+    if ((st = fcg_solve(P, w, lowp, s, bnorm, rtol, max_iter, kFcgInnerRtol, rr_stall, &iters, &outer, &converged,
+                        &rel)) != EHYB_OK)
+      return st;
+    info->relres_recursive = rel;
+    info->flexible = 1;
   }
   // true residual in FP64, then x back to the original numbering
   CKC(launch_ehyb_f64(D, w->xp, w->q, 0, s));

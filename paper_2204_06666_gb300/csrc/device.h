@@ -9,10 +9,11 @@ namespace ehyb {
 // PositionELL, ell_col = ColELL, ell_val = ValELL, er_row = yIdxER).
 struct DevPlan {
   int64_t n = 0;
+  int64_t n_x = 0;  // elements of x the extra-row columns index; 0 = n (a shard's x holds its halo too)
   int32_t nparts = 0, tpr = 1, er_tpr = 1, threads = 512;
   int32_t max_part_rows = 0;
   int32_t kbatch = 8;  // FP64 batch depth (two pipelined half-batches): 6 on wide slices (>= 32 slots a lane), else 8;
-                       // the FP32 / BF16 kernels always hold 12
+                       // the FP32 / BF16 kernels hold 12 (column-major copies) or 16 (copies in 4-slot groups)
   const int32_t* new_to_old = nullptr;
   const int32_t* part_ptr = nullptr;
   const int32_t* slice_ptr = nullptr;
@@ -36,6 +37,12 @@ struct DevPlan {
   const double* er_sval = nullptr;
   const float* er_sval_f32 = nullptr;
   const uint16_t* er_sval_bf16 = nullptr;
+  // slot layout of the FP32 / BF16 copies (1: column-major like the FP64 arrays; 4: runs of four slots per
+  // lane, with these column arrays in the same layout; for group 1 they alias the FP64 layout's columns)
+  int32_t lowp_group = 1;
+  const uint16_t* ell_col_low = nullptr;
+  const int32_t* er_scol_low = nullptr;
+  const int32_t* er_scol_old_low = nullptr;
   int32_t* status = nullptr;  // device status word (first fault wins)
   uint64_t wait_timeout_ns = 1000000000ull;
   int32_t inject_wait_fault = 0;

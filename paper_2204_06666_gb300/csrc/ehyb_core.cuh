@@ -9,8 +9,10 @@
 //        EHYB_ERR_TIMEOUT in the plan status word and returns);
 //     3. each warp takes 32-lane slices of the partition from a shared counter (the dynamic
 //        slice balancing of Alg. 3) and runs y[row] = sum_k ValELL * CachedVec[ColELL] with the
-//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot, eight slots of
-//        values and columns loaded ahead of their FMAs to keep enough bytes in flight;
+//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot, six to twelve slots of
+//        values and columns loaded ahead of their FMAs to keep enough bytes in flight; the FP32 / BF16
+//        copies of plans with wide slices keep each lane's slots in runs of four (slot_pos in
+//        plan.h) and read a run's values and columns with one vector load each;
 //     4. extra-row (ER) entries, two layouts:
 //        - sliced (er_layout 0, default): the ER entries of the slice's own rows are stored in
 //          the same lane -> row arrangement right behind it (the paper stores its ER part as
@@ -144,6 +146,8 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(
 constexpr int kBatch = 8;   // slots whose loads are issued before their FMAs (default batch depth)
 constexpr int kStage = 16;  // elements of x per thread in flight while a slice of x is gathered
 
+// ---- column-major slots (Alg. 2: slot k of a lane at 32 k from its first one)
+
 // acc += sum_{k<w} v[32k] * xs[c[32k]]: slab slots of one lane, x from shared memory.  Loads go out in
 // half-batches of KB/2 slots, the next half-batch issued before the current one's FMAs (KB slots held in
 // registers); the FMAs run in slot order, so the result does not depend on KB.  (A predicated last batch
@@ -212,9 +216,145 @@ __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __r
   return acc;
 }
 
+// ---- slots in runs of four per lane (the FP32 / BF16 copies of plans with wide slices; slot_pos, group 4):
+// a lane reads a run's four values with one 16-byte (FP32) or 8-byte (BF16) load and its four 16-bit columns
+// with one 8-byte load; the w mod 4 slots after the runs are column-major.
+constexpr int kGroup = 4;
+constexpr int kErGroups = 2;  // runs per batch of the extra-row loop (8 slots, their x gathers in flight)
+
+__device__ __forceinline__ void ld_group(const float* p, float (&o)[4]) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = a.z;
+  o[3] = a.w;
+}
+__device__ __forceinline__ void ld_group(const uint16_t* p, float (&o)[4]) {  // four BF16 values
+  const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+  o[0] = __uint_as_float(v.x << 16);  // the value at the lower address is the low half (little endian)
+  o[1] = __uint_as_float(v.x & 0xffff0000u);
+  o[2] = __uint_as_float(v.y << 16);
+  o[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+__device__ __forceinline__ void ld_cols(const uint16_t* p, int (&c)[4]) {  // four 16-bit columns
+  const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+  c[0] = (int)(v.x & 0xffffu);
+  c[1] = (int)(v.x >> 16);
+  c[2] = (int)(v.y & 0xffffu);
+  c[3] = (int)(v.y >> 16);
+}
+__device__ __forceinline__ void ld_cols(const int32_t* p, int (&c)[4]) {  // four 32-bit columns
+  const int4 v = __ldcs(reinterpret_cast<const int4*>(p));
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
+  c[3] = v.w;
+}
+
+// slab_dot on runs of four: vb, cb = the slice's first slot; half-batches of KB/8 runs (KB slots in flight),
+// then the column-major tail.  Same slot order, same result as slab_dot on the column-major copy.
+template <typename V, typename X, int KB>
+__device__ __forceinline__ X slab_dot_runs(const V* __restrict__ vb, const uint16_t* __restrict__ cb, int lane, int w,
+                                           const X* xs, X acc, int lim, int32_t* status) {
+  constexpr int NG = KB / 8;
+  static_assert(NG >= 1 && KB % 8 == 0, "runs: half-batches of whole runs");
+  const int ng = w >> 2;
+  const V* vp = vb + kGroup * lane;  // run g of this lane: vp + 128 g
+  const uint16_t* cp = cb + kGroup * lane;
+  int g = 0;
+  if (ng >= NG) {
+    X va[NG][kGroup];
+    int ca[NG][kGroup];
+#pragma unroll
+    for (int u = 0; u < NG; ++u) {
+      ld_group(vp + 128 * (int64_t)u, va[u]);
+      ld_cols(cp + 128 * (int64_t)u, ca[u]);
+    }
+    for (g = NG; g + NG <= ng; g += NG) {
+      X vn[NG][kGroup];
+      int cn[NG][kGroup];
+#pragma unroll
+      for (int u = 0; u < NG; ++u) {
+        ld_group(vp + 128 * (int64_t)(g + u), vn[u]);
+        ld_cols(cp + 128 * (int64_t)(g + u), cn[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < NG; ++u)
+#pragma unroll
+        for (int t = 0; t < kGroup; ++t) acc = fma_t(va[u][t], xs[checked(ca[u][t], lim, status)], acc);
+#pragma unroll
+      for (int u = 0; u < NG; ++u)
+#pragma unroll
+        for (int t = 0; t < kGroup; ++t) {
+          va[u][t] = vn[u][t];
+          ca[u][t] = cn[u][t];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NG; ++u)
+#pragma unroll
+      for (int t = 0; t < kGroup; ++t) acc = fma_t(va[u][t], xs[checked(ca[u][t], lim, status)], acc);
+  }
+  for (; g < ng; ++g) {  // fewer than NG whole runs left
+    X v[kGroup];
+    int c[kGroup];
+    ld_group(vp + 128 * (int64_t)g, v);
+    ld_cols(cp + 128 * (int64_t)g, c);
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t) acc = fma_t(v[t], xs[checked(c[t], lim, status)], acc);
+  }
+  // column-major tail: slot k (k >= 4 ng) of this lane at the slice's first slot + 32 k + lane
+  return slab_dot<V, X, 2>(vb + 128 * (int64_t)ng + lane, cb + 128 * (int64_t)ng + lane, w & (kGroup - 1), xs, acc,
+                           lim, status);
+}
+
+// er_dot on runs of four: batches of kErGroups runs (values and columns loaded, then their x gathers, then
+// the FMAs in slot order), then the remaining run and the column-major tail
+template <typename V, typename X>
+__device__ __forceinline__ X er_dot_runs(const V* __restrict__ vb, const int32_t* __restrict__ cb, int lane, int w,
+                                         const X* __restrict__ xg, X acc, int64_t lim, int32_t* status) {
+  constexpr int NB = kErGroups;
+  const int ng = w >> 2;
+  const V* vp = vb + kGroup * lane;
+  const int32_t* cp = cb + kGroup * lane;
+  int g = 0;
+  for (; g + NB <= ng; g += NB) {
+    X v[NB][kGroup];
+    int c[NB][kGroup];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      ld_group(vp + 128 * (int64_t)(g + u), v[u]);
+      ld_cols(cp + 128 * (int64_t)(g + u), c[u]);
+    }
+    X xv[NB][kGroup];
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+#pragma unroll
+      for (int t = 0; t < kGroup; ++t) xv[u][t] = __ldg(xg + checked(c[u][t], lim, status));
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+#pragma unroll
+      for (int t = 0; t < kGroup; ++t) acc = fma_t(v[u][t], xv[u][t], acc);
+  }
+  for (; g < ng; ++g) {
+    X v[kGroup];
+    int c[kGroup];
+    ld_group(vp + 128 * (int64_t)g, v);
+    ld_cols(cp + 128 * (int64_t)g, c);
+    X xv[kGroup];
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t) xv[t] = __ldg(xg + checked(c[t], lim, status));
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t) acc = fma_t(v[t], xv[t], acc);
+  }
+  return er_dot<V, X, 2>(vb + 128 * (int64_t)ng + lane, cb + 128 * (int64_t)ng + lane, w & (kGroup - 1), xg, acc,
+                         lim, status);
+}
+
 struct KArgs {
   int32_t tpr_log2, er_tpr_log2;
-  int64_t n;              // rows (= columns) of the matrix
+  int64_t n;              // rows of the matrix (of y)
+  int64_t n_x;            // elements of x the extra-row columns index (n; a shard adds its halo)
   int64_t smem_elems;     // capacity of the staged slice of x (elements); checked build only
   const int64_t* er_slice_pos;
   const int32_t* er_scol;
@@ -281,7 +421,7 @@ struct BlockState {
 // Returns false (uniformly across the block) when the staging wait ran
 // out of time.
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false, bool GATHER = false,
-          int KB = kBatch>
+          int KB = kBatch, bool RUNS = false>
 __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
                                                const V* __restrict__ er_val, const X* __restrict__ xp,
                                                X* __restrict__ y, const int p, X* xs, BlockState& bs) {
@@ -391,10 +531,18 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
         nwe = (int)((a.er_slice_pos[nxt + 1] - nepos) >> 5);
       }
     }
-    X acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0), pe - pb, a.status);
-    if (ER_SLICED)
-      acc = er_dot<V, X, KB>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc,
-                             a.n, a.status);
+    X acc;
+    if constexpr (RUNS) {  // the copy in runs of four slots (its own column arrays are in a.ell_col / a.er_scol*)
+      acc = slab_dot_runs<V, X, KB>(ell_val + pos, a.ell_col + pos, lane, w, xsl, X(0), pe - pb, a.status);
+      if (ER_SLICED)
+        acc = er_dot_runs<V, X>(er_val + epos, (GATHER ? a.er_scol_old : a.er_scol) + epos, lane, we, xp, acc, a.n_x,
+                                a.status);
+    } else {
+      acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0), pe - pb, a.status);
+      if (ER_SLICED)
+        acc = er_dot<V, X, KB>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc,
+                               a.n_x, a.status);
+    }
     for (int off = tpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     const int row = pb + (s - s0) * rows_per_slice + (lane >> a.tpr_log2);
     if (sub == 0 && row < pe) {
@@ -481,6 +629,7 @@ inline KArgs make_kargs(const DevPlan& P) {
   KArgs a;
   a.tpr_log2 = ilog2(P.tpr);
   a.n = P.n;
+  a.n_x = P.n_x > 0 ? P.n_x : P.n;
   a.smem_elems = (int64_t)P.max_part_rows + 2;  // launches set the exact capacity of their shared memory
   a.er_tpr_log2 = ilog2(P.er_tpr);
   a.er_slice_pos = P.er_slice_pos;

@@ -52,22 +52,57 @@ uint16_t f32_to_bf16_rne(float f) {
   return (uint16_t)((u + bias) >> 16);
 }
 
-void make_lowp_copies(HostPlan& P, int lowp) {
+double mean_slice_width(const HostPlan& P) {
+  const double slots = (double)(P.slice_pos.empty() ? 0 : P.slice_pos.back()) +
+                       (double)(P.er_slice_pos.empty() ? 0 : P.er_slice_pos.back());
+  return P.nslices ? slots / (32.0 * (double)P.nslices) : 0.0;
+}
+
+void make_lowp_copies(HostPlan& P, int lowp, int group) {
+  if (lowp == 0) return;
+  if (group == 0) group = mean_slice_width(P) >= 32.0 ? kSlotGroup : 1;
+  if (P.er_layout != 0) group = 1;  // the run loops read the sliced extra-row layout only
+  P.lowp_group = group;
   const size_t stored = P.ell_val.size(), er_nnz = P.er_val.size(), er_stored = P.er_sval.size();
+  // destination of every column-major slot (identity in group 1)
+  auto regroup = [&](const std::vector<int64_t>& pos, size_t total, std::vector<int64_t>& dst) {
+    dst.resize(total);
+    for (int32_t s = 0; s < P.nslices; ++s) {
+      const int64_t base = pos[(size_t)s];
+      const int32_t w = (int32_t)((pos[(size_t)s + 1] - base) / 32);
+      for (int32_t k = 0; k < w; ++k)
+        for (int32_t lane = 0; lane < 32; ++lane)
+          dst[(size_t)(base + 32 * (int64_t)k + lane)] = slot_pos(base, w, k, lane, group);
+    }
+  };
+  std::vector<int64_t> sd, ed;
+  if (group != 1) {
+    regroup(P.slice_pos, stored, sd);
+    if (P.er_layout == 0) regroup(P.er_slice_pos, er_stored, ed);
+    P.ell_col_low.resize(stored);
+    for (size_t k = 0; k < stored; ++k) P.ell_col_low[(size_t)sd[k]] = P.ell_col[k];
+    P.er_scol_low.resize(er_stored);
+    P.er_scol_old_low.resize(er_stored);
+    for (size_t k = 0; k < er_stored; ++k) {
+      P.er_scol_low[(size_t)ed[k]] = P.er_scol[k];
+      P.er_scol_old_low[(size_t)ed[k]] = P.er_scol_old[k];
+    }
+  }
+  auto at = [&](const std::vector<int64_t>& d, size_t k) { return d.empty() ? k : (size_t)d[k]; };
   if (lowp == 1) {
     P.ell_val_f32.resize(stored);
     P.er_val_f32.resize(er_nnz);
     P.er_sval_f32.resize(er_stored);
-    for (size_t k = 0; k < stored; ++k) P.ell_val_f32[k] = (float)P.ell_val[k];
+    for (size_t k = 0; k < stored; ++k) P.ell_val_f32[at(sd, k)] = (float)P.ell_val[k];
     for (size_t k = 0; k < er_nnz; ++k) P.er_val_f32[k] = (float)P.er_val[k];
-    for (size_t k = 0; k < er_stored; ++k) P.er_sval_f32[k] = (float)P.er_sval[k];
+    for (size_t k = 0; k < er_stored; ++k) P.er_sval_f32[at(ed, k)] = (float)P.er_sval[k];
   } else if (lowp == 2) {
     P.ell_val_bf16.resize(stored);
     P.er_val_bf16.resize(er_nnz);
     P.er_sval_bf16.resize(er_stored);
-    for (size_t k = 0; k < stored; ++k) P.ell_val_bf16[k] = f32_to_bf16_rne((float)P.ell_val[k]);
+    for (size_t k = 0; k < stored; ++k) P.ell_val_bf16[at(sd, k)] = f32_to_bf16_rne((float)P.ell_val[k]);
     for (size_t k = 0; k < er_nnz; ++k) P.er_val_bf16[k] = f32_to_bf16_rne((float)P.er_val[k]);
-    for (size_t k = 0; k < er_stored; ++k) P.er_sval_bf16[k] = f32_to_bf16_rne((float)P.er_sval[k]);
+    for (size_t k = 0; k < er_stored; ++k) P.er_sval_bf16[at(ed, k)] = f32_to_bf16_rne((float)P.er_sval[k]);
   }
 }
 
@@ -671,7 +706,7 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     ell_part[(size_t)piece.fetch_add(1)] = ell_sum;
   });
   for (int64_t v : ell_part) P.ell_nnz += v;
-  make_lowp_copies(P, prm.lowp);
+  make_lowp_copies(P, prm.lowp, prm.lowp_group);
   P.reorder_ms = now_ms() - t1;
   return 0;
 }

@@ -8,12 +8,27 @@
 
 namespace ehyb {
 
+// Slot layouts of a slice (slab: Alg. 2's ValELL / ColELL; the sliced ER part alike).  A slice of width w
+// (slots per lane) stores its 32 x w slots from `base` on (a multiple of 32).
+//   group 1 (Alg. 2, the FP64 arrays): slot k of lane L at base + 32 k + L (column-major);
+//   group 4 (the FP32 / BF16 copies of plans with wide slices): the first wg = 4 floor(w / 4) slots of each
+//     lane in runs of four, slot k < wg of lane L at base + 128 (k / 4) + 4 L + k % 4, so a lane reads four
+//     values with one vector load (16 bytes of FP32, 8 of BF16; four 16-bit columns in 8 bytes); the last
+//     w - wg slots column-major as in group 1.  Every run is aligned to its own size.
+constexpr int kSlotGroup = 4;
+inline int64_t slot_pos(int64_t base, int32_t w, int32_t k, int32_t lane, int32_t group) {
+  const int32_t wg = group == kSlotGroup ? (w & ~(kSlotGroup - 1)) : 0;
+  return k < wg ? base + 32 * kSlotGroup * (int64_t)(k / kSlotGroup) + kSlotGroup * lane + (k % kSlotGroup)
+                : base + 32 * (int64_t)k + lane;
+}
+
 struct PlanParams {
   int64_t n = 0;
   int32_t slice_rows = 0;     // hard cap on rows per partition (VecSize), resolved before build
   int32_t ell_width_cap = 0;  // 0 = unlimited
   int32_t ell_tpr = 1;        // lanes per row in a slab slice
   int32_t lowp = 0;           // 0 none, 1 fp32, 2 bf16 value copies
+  int32_t lowp_group = 0;     // slot layout of the value copies: 1, 4, or 0 = 4 on wide slices (make_lowp_copies)
   int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR
   const int32_t* part_vec = nullptr;
   int32_t threads = 0;        // host threads for the parallel phases (0 = the machine's); results do not depend on it
@@ -52,6 +67,11 @@ struct HostPlan {
   std::vector<float> er_sval_f32;
   std::vector<uint16_t> er_sval_bf16;
   std::vector<int32_t> row_er_count;
+  // slot layout of the FP32 / BF16 copies (slot_pos group); with group 4 they come with their own slab and
+  // sliced-ER column arrays in that layout (the FP64 arrays stay column-major)
+  int32_t lowp_group = 1;
+  std::vector<uint16_t> ell_col_low;
+  std::vector<int32_t> er_scol_low, er_scol_old_low;
   int64_t er_nnz = 0;
   int64_t ell_nnz = 0;
   int32_t max_part_rows = 0;
@@ -59,8 +79,13 @@ struct HostPlan {
 };
 
 // FP32 (lowp 1) or BF16 (lowp 2) copies of the FP64 slab and ER values (FP64 -> FP32 -> BF16, round to
-// nearest even at each step); lowp 0 does nothing
-void make_lowp_copies(HostPlan& P, int lowp);
+// nearest even at each step); lowp 0 does nothing.  group: their slot layout (1 or 4; 0 = 4 when a slice
+// holds 32 or more slab + sliced-ER slots per lane on average, else 1); with 4 the columns are copied into
+// that layout too.
+void make_lowp_copies(HostPlan& P, int lowp, int group = 0);
+
+// mean slab + sliced-ER slots per lane of a slice
+double mean_slice_width(const HostPlan& P);
 
 // Eq. 1 and Eq. 2: smallest K >= 1 with n*tau/(K*P) < budget (and at most 2^16 rows so the
 // 16-bit column offset holds); returns VecSize = ceil(n / (K*P)).

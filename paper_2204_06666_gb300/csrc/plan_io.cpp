@@ -303,6 +303,7 @@ extern "C" ehyb_status_t ehyb_plan_load(const char* path, const ehyb_options_t* 
   else ehyb_options_default(&opt);
   auto pow2_or_zero = [](int32_t v) { return v == 0 || (v >= 1 && v <= 32 && (v & (v - 1)) == 0); };
   if (opt.lowp < 0 || opt.lowp > 2 || !pow2_or_zero(opt.er_tpr) || opt.num_sms < 0 || opt.wait_timeout_ns < 0 ||
+      (opt.lowp_group != 0 && opt.lowp_group != 1 && opt.lowp_group != 4) ||
       (opt.block_threads != 0 && (opt.block_threads < 32 || opt.block_threads > 1024 || opt.block_threads % 32)))
     return EHYB_ERR_INVALID_ARG;
   File f(std::fopen(path, "rb"));
@@ -347,7 +348,7 @@ extern "C" ehyb_status_t ehyb_plan_load(const char* path, const ehyb_options_t* 
   if (!ok || fnv.done() != h.checksum || !valid(H, h)) return EHYB_ERR_IO;
   H.old_to_new.assign((size_t)H.n, 0);
   for (int64_t r = 0; r < H.n; ++r) H.old_to_new[(size_t)H.new_to_old[(size_t)r]] = (int32_t)r;
-  make_lowp_copies(H, opt.lowp);
+  make_lowp_copies(H, opt.lowp, opt.lowp_group);
 
   int dev = 0, sms = 0, optin = 0;
   if (opt.host_only) {

@@ -14,10 +14,12 @@ namespace {
 using namespace core;
 
 // batch depth of the FP32 / BF16 kernels: a 4- or 2-byte value needs more slots in flight than an FP64 one
-// (12 measured best among 8, 12, 16 and 24: tet 126^3 FP32 50.0 -> 49.0 us, BF16 52.0 -> 48.2 us)
+// (12 measured best among 8, 12, 16 and 24: tet 126^3 FP32 50.0 -> 49.0 us, BF16 52.0 -> 48.2 us); 16 (four
+// runs of four) on copies laid out in runs
 constexpr int kLowBatch = 12;
+constexpr int kRunBatch = 16;
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false,
-          int KB = (sizeof(V) == 8 ? kBatch : kLowBatch)>
+          int KB = (sizeof(V) == 8 ? kBatch : kLowBatch), bool RUNS = false>
 __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
                                                     const V* __restrict__ er_val, const X* __restrict__ xp,
                                                     X* __restrict__ y) {
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     bs.bar_ready = 0;
     bs.phase = 0;
   }
-  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB>(a, ell_val, er_val, xp, y, blockIdx.x,
+  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB, RUNS>(a, ell_val, er_val, xp, y, blockIdx.x,
                                                             reinterpret_cast<X*>(smem_raw), bs);
 }
 
@@ -95,6 +97,13 @@ static cudaError_t set_smem(int bytes) {
     if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false, false, kWideBatch>, attr, bytes))) return e;
     if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, false, kWideBatch>, attr, bytes))) return e;
   }
+  if constexpr (!std::is_same<V, double>::value) {  // the copies laid out in runs of four (sliced ER layout)
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, false, kRunBatch, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false, false, kRunBatch, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true, kRunBatch, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, true, true, kRunBatch, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true, false, kRunBatch, true>, attr, bytes))) return e;
+  }
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false>, attr, bytes))) return e;
@@ -127,9 +136,12 @@ cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, fl
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false>
 static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArgs& a, const V* ev, const V* erv,
                        const X* xp, X* y) {
-  // FP64 kernels on plans with wide slices use the shallower batch (sliced-ER layout only)
+  // FP64 kernels on plans with wide slices use the shallower batch (sliced-ER layout only); FP32 / BF16
+  // copies laid out in runs of four use the run loops
   constexpr bool kWideOk = std::is_same<V, double>::value && ER_SLICED;
+  constexpr bool kRunsOk = !std::is_same<V, double>::value && ER_SLICED;
   const bool wide = kWideOk && P.kbatch == kWideBatch;
+  const bool runs = kRunsOk && P.lowp_group == 4;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)P.nparts);
   cfg.blockDim = dim3((unsigned)P.threads);
@@ -140,9 +152,20 @@ static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArg
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (wide) cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kWideOk ? kWideBatch : kBatch>,
-                                a, ev, erv, xp, y);
-  else cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
+  if (wide) {
+    cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kWideOk ? kWideBatch : kBatch>, a, ev,
+                       erv, xp, y);
+  } else if (runs) {
+    KArgs ar = a;  // the copies' own column arrays, in the same runs
+    ar.ell_col = P.ell_col_low;
+    ar.er_scol = P.er_scol_low;
+    ar.er_scol_old = P.er_scol_old_low;
+    cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kRunsOk ? kRunBatch : kLowBatch,
+                                         kRunsOk>,
+                       ar, ev, erv, xp, y);
+  } else {
+    cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
+  }
 }
 
 template <typename V, typename X>

@@ -113,7 +113,7 @@ def test_cg_not_converged_status(eh):
     assert st == 0 and info["iterations"] == 0 and np.all(x == 0)
 
 
-@pytest.mark.parametrize("refine,lowp", [(1, 1), (2, 2), (3, 1), (4, 2)])
+@pytest.mark.parametrize("refine,lowp", [(1, 1), (2, 2), (3, 1), (4, 2), (5, 1), (6, 2)])
 def test_refined_cg_reaches_fp64_accuracy(eh, refine, lowp):
     A = gen.tet_lap3d(N=24)
     xstar = gen.uniform(A.n, 23)
@@ -128,6 +128,37 @@ def test_refined_cg_reaches_fp64_accuracy(eh, refine, lowp):
     assert err <= 1e-7
 
 
+@pytest.mark.parametrize("refine", [6, 4])
+def test_bf16_values_on_clamped_elasticity_reach_1e10(eh, refine):
+    # clamped Q1 elasticity: u_bf16 kappa(A) is not small, so refinement around a BF16 solve can stall; the
+    # flexible FP64 CG (refine 6, or taking over refine 4) keeps the BF16 solve as a preconditioner only
+    A = gen.hex_elast3d(N=14, clamp_minz=True)
+    xstar = gen.uniform(A.n, 24)
+    b = oracle.spmv(A, xstar)
+    P, st, info, x = _solve(eh, A, b, rtol=1e-10, max_iter=40000, refine=refine, lowp=2)
+    rel = _true_relres(A, b, x)                          # the FP64 residual, recomputed by the oracle
+    assert st == 0 and info["converged"] == 1 and rel <= 1e-10, info
+    assert abs(info["relres"] - rel) <= 1e-12
+    if refine == 6:
+        assert info["flexible"] == 1 and info["refinements"] >= 2
+    xo = oracle.cg(A, b, rtol=1e-12, max_iter=40000)[0]
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-6   # stated error against the FP64 oracle solve
+
+
+def test_flexible_cg_is_deterministic(eh):
+    A = gen.tet_lap3d(N=16)
+    b = oracle.spmv(A, gen.uniform(A.n, 3))
+    P = eh.Plan(A, lowp=2)
+    bd = torch.from_numpy(b).cuda()
+    outs = []
+    for _ in range(2):
+        xd = torch.zeros_like(bd)
+        st, info = P.cg(bd, xd, rtol=1e-10, max_iter=20000, refine=6)
+        assert st == 0
+        outs.append((xd.cpu().numpy(), info["iterations"], info["refinements"]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
+
+
 def test_cg_option_errors(eh):
     A = gen.tet_lap3d(N=10)
     b = torch.ones(A.n, dtype=torch.float64, device="cuda")
@@ -136,6 +167,12 @@ def test_cg_option_errors(eh):
     with pytest.raises(eh.EhybError) as e:
         P.cg(b, x, refine=1)          # no FP32 value copy in this plan
     assert e.value.status == 7
+    with pytest.raises(eh.EhybError) as e:
+        P.cg(b, x, refine=6)          # no BF16 value copy either
+    assert e.value.status == 7
+    with pytest.raises(eh.EhybError) as e:
+        P.cg(b, x, refine=7)
+    assert e.value.status == 1
     Q = eh.Plan(A, er_layout=1)
     with pytest.raises(eh.EhybError) as e:
         Q.cg(b, x)                    # the fused dot needs the sliced ER layout

@@ -258,6 +258,39 @@ def test_lowp_integer_exact_and_fem_bound(eh, lowp):
     assert np.all(np.abs(yd.cpu().numpy() - ref) <= bound)
 
 
+@pytest.mark.parametrize("lowp", [1, 2])
+@pytest.mark.parametrize("make", [lambda: gen.hex_elast3d(N=14), lambda: gen.tet_lap3d(N=20),
+                                  lambda: gen.random_csr(3000, 7, mean_row=40, int_values=True, long_rows=3,
+                                                         long_len=900, empty_frac=0.02)],
+                         ids=["hex", "tet", "ragged_int"])
+def test_lowp_runs_layout_bit_identical_to_column_major(eh, lowp, make):
+    # the copies in runs of four slots (lowp_group 4) sum every row in the same slot order as the column-major
+    # copies (lowp_group 1): identical bits, for the fused-permutation entry and inside the FP32 CG
+    A = make()
+    x = gen.uniform(A.n, 4).astype(np.float32)
+    out = {}
+    for grp in (1, 4):
+        P = eh.Plan(A, lowp=lowp, lowp_group=grp, slice_rows=400)
+        assert P.info()["lowp_group"] == grp
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.full_like(xd, np.nan)
+        P.spmv_lowp(xd, yd)
+        torch.cuda.synchronize()
+        assert P.check() == 0
+        out[grp] = yd.cpu().numpy()
+    assert np.array_equal(out[1], out[4])
+
+
+def test_lowp_group_auto_follows_slice_width(eh):
+    # 32 or more slab + sliced-ER slots per lane on average (elasticity): runs; the narrow tet slices: column-major
+    assert eh.Plan(gen.hex_elast3d(N=14), lowp=2).info()["lowp_group"] == 4
+    assert eh.Plan(gen.tet_lap3d(N=20), lowp=2).info()["lowp_group"] == 1
+    assert eh.Plan(gen.hex_elast3d(N=14), lowp=2, er_layout=1).info()["lowp_group"] == 1
+    with pytest.raises(eh.EhybError) as e:
+        eh.Plan(gen.tet_lap3d(N=8), lowp=1, lowp_group=2)
+    assert e.value.status == 1
+
+
 def test_lowp_requires_lowp_plan(eh):
     A = gen.fem2d_p1(N=20)
     P = eh.Plan(A)

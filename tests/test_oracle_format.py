@@ -10,10 +10,11 @@ import gen
 from oracle import ehyb_format as ef
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ehyb_tiny.json")
+GROUPED = os.path.join(os.path.dirname(__file__), "golden", "ehyb_grouped.json")
 
 
-def golden_plan():
-    g = json.load(open(GOLDEN))
+def golden_plan(path=GOLDEN):
+    g = json.load(open(path))
     p = dict(g["plan"])
     size = p["slice_pos"][-1]
     col = np.zeros(size, np.uint16)
@@ -26,13 +27,15 @@ def golden_plan():
     return g, p, A
 
 
-def test_decode_hand_derived_example():
-    g, p, A = golden_plan()
+@pytest.mark.parametrize("path", [GOLDEN, GROUPED], ids=["tiny", "grouped"])
+def test_decode_hand_derived_example(path):
+    g, p, A = golden_plan(path)
     assert ef.same_multiset(ef.decode(p), ef.triplets(A))
 
 
-def test_decode_hand_derived_example_sliced_extra_rows():
-    g, p, A = golden_plan()
+@pytest.mark.parametrize("path", [GOLDEN, GROUPED], ids=["tiny", "grouped"])
+def test_decode_hand_derived_example_sliced_extra_rows(path):
+    g, p, A = golden_plan(path)
     q = {k: v for k, v in p.items() if not k.startswith("er_")}
     q["er_layout"] = 0
     q["er_slice_pos"] = p["er_slice_pos"]
@@ -42,8 +45,55 @@ def test_decode_hand_derived_example_sliced_extra_rows():
     for pos, c, v in p["er_slice_entries"]:
         q["er_scol"][pos], q["er_sval"][pos] = c, v
     assert ef.same_multiset(ef.decode(q), ef.triplets(A))
-    q["row_er_count"] = [0, 1, 0, 0, 0]   # the extra entry attributed to the wrong row is dropped
+    q["row_er_count"] = np.roll(np.asarray(p["row_er_count"]), 1)   # extra entries attributed to the wrong row
     assert not ef.same_multiset(ef.decode(q), ef.triplets(A))
+
+
+def test_slot_index_runs_and_tail():
+    # group 1 is Alg. 2's column-major order
+    assert [ef.slot_index(0, 6, k, 5) for k in range(6)] == [5, 37, 69, 101, 133, 165]
+    # group 4, width 6: slots 0..3 of a lane are four consecutive words, the 32 lanes' runs side by side;
+    # slots 4, 5 are column-major behind the runs
+    assert [ef.slot_index(0, 6, k, 0, 4) for k in range(6)] == [0, 1, 2, 3, 128, 160]
+    assert [ef.slot_index(0, 6, k, 5, 4) for k in range(6)] == [20, 21, 22, 23, 133, 165]
+    # narrower than a run: column-major in both layouts
+    assert [ef.slot_index(32, 3, k, 7, 4) for k in range(3)] == [39, 71, 103]
+    # every run is aligned to four slots, so a 4-slot vector load of it is aligned to its own size
+    assert all(ef.slot_index(0, 9, 4 * q, lane, 4) % 4 == 0 for q in range(2) for lane in range(32))
+
+
+@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("width", range(0, 11))
+def test_slot_index_fills_the_slice_once_in_both_layouts(width, group):
+    got = sorted(ef.slot_index(64, width, k, lane, group) for lane in range(32) for k in range(width))
+    assert got == list(range(64, 64 + 32 * width))
+
+
+def _runs_plan():
+    # the grouped golden with its FP32 copy (integer values: exact) in place of the FP64 arrays
+    g, p, A = golden_plan(GROUPED)
+    q = dict(p)
+    size, esize = p["slice_pos"][-1], p["er_slice_pos"][-1]
+    q["ell_col"], q["ell_val"] = np.zeros(size, np.uint16), np.zeros(size)
+    for pos, c, v in g["runs"]["ell_entries"]:
+        q["ell_col"][pos], q["ell_val"][pos] = c, v
+    q["er_layout"], q["er_scol"], q["er_sval"] = 0, np.full(esize, p["er_slice_pad_col"][0], np.int32), np.zeros(esize)
+    for pos, c, v in g["runs"]["er_slice_entries"]:
+        q["er_scol"][pos], q["er_sval"][pos] = c, v
+    return q, A
+
+
+def test_decode_runs_layout_of_the_hand_derived_example():
+    q, A = _runs_plan()
+    assert ef.same_multiset(ef.decode(q, group=4), ef.triplets(A))
+    assert not ef.same_multiset(ef.decode(q, group=1), ef.triplets(A))   # read in the wrong layout
+
+
+def test_decode_detects_a_swapped_pair_inside_a_run():
+    q, A = _runs_plan()
+    q["ell_val"] = q["ell_val"].copy()
+    q["ell_val"][[4, 128]] = q["ell_val"][[128, 4]]   # slot 0 of lane 1 swapped with slot 4 of lane 0
+    assert not ef.same_multiset(ef.decode(q, group=4), ef.triplets(A))
 
 
 def test_decode_detects_a_misplaced_entry():

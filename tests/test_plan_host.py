@@ -8,7 +8,7 @@ import pytest
 import gen
 from oracle import ehyb_format as ef
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ehyb_tiny.json")
+GOLDENS = [os.path.join(os.path.dirname(__file__), "golden", f) for f in ("ehyb_tiny.json", "ehyb_grouped.json")]
 
 
 def _plan(A, **kw):
@@ -16,8 +16,9 @@ def _plan(A, **kw):
     return eh.Plan(A, host_only=1, **kw)
 
 
-def test_golden_plan_matches_hand_derivation_exactly():
-    g = json.load(open(GOLDEN))
+@pytest.mark.parametrize("golden", GOLDENS, ids=["tiny", "grouped"])
+def test_golden_plan_matches_hand_derivation_exactly(golden):
+    g = json.load(open(golden))
     A = gen.CSR(g["n"], np.array(g["row_ptr"], np.int64), np.array(g["col"], np.int32), np.array(g["val"], float))
     want_col = np.zeros(g["plan"]["slice_pos"][-1], np.uint16)
     want_val = np.zeros(g["plan"]["slice_pos"][-1])
@@ -42,6 +43,20 @@ def test_golden_plan_matches_hand_derivation_exactly():
     for pos, c, v in g["plan"]["er_slice_entries"]:
         scol[pos], sval[pos] = c, v
     assert np.array_equal(ex["er_scol"], scol) and np.array_equal(ex["er_sval"], sval)
+    assert ef.same_multiset(ef.decode(ex), ef.triplets(A))
+    # the FP32 copy in runs of four slots (hand-derived positions where the golden gives them)
+    ex = _plan(A, part_vec=g["part_vec"], lowp=1, lowp_group=4).export()
+    assert ex["lowp_group"] == 4
+    assert ef.same_multiset(ef.decode(ef.low_values(ex), group=4), ef.triplets(A))   # integer values: exact
+    if "runs" in g:
+        want_col[:], want_val[:] = 0, 0
+        for pos, c, v in g["runs"]["ell_entries"]:
+            want_col[pos], want_val[pos] = c, v
+        assert np.array_equal(ex["ell_col_low"], want_col) and np.array_equal(ex["ell_val_low"], want_val)
+        scol[:], sval[:] = g["plan"]["er_slice_pad_col"][0], 0
+        for pos, c, v in g["runs"]["er_slice_entries"]:
+            scol[pos], sval[pos] = c, v
+        assert np.array_equal(ex["er_scol_low"], scol) and np.array_equal(ex["er_sval_low"], sval)
 
 
 def _invariants(A, ex, cap=None, width_cap=0):
