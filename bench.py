@@ -24,11 +24,12 @@ with the warm time in `warm`.  Also reported:
     under `multicore` whole products split over every host core.
 
 Other modes: --partitioner 1 (multilevel partition), --lowp (FP32 / BF16 SpMVs), --solver (CG,
-mixed precision, FSAI-PCG to 1e-10), --transient (implicit time steps reusing one plan),
---batch, --spmm, --plan-io.  --impl reference times the oracle on the host cores as the reference
-arm (there is no runnable reference code).  Multi-GPU (torchrun): independent replicas, one per
-rank ("replicas only": the method's kernel has no exchange step at one GPU per rank), max time
-over ranks.
+mixed precision, flexible CG, FSAI-PCG to 1e-10), --transient (implicit time steps reusing one plan),
+--batch, --spmm, --plan-io, --shard (row shards with a halo exchange per product across the torchrun
+ranks: strong scaling of one matrix).  --impl reference times the oracle on the host cores as the reference
+arm (there is no runnable reference code).  Multi-GPU (torchrun): by default independent replicas, one
+full product per rank (weak scaling, max time over ranks); with --shard one matrix split into row shards,
+its halo moved by an NCCL all-to-all every product (strong scaling).
 """
 from __future__ import annotations
 
@@ -362,7 +363,7 @@ def run_ehyb(args):
         long_window = {"steps": LONG_WINDOW_STEPS, "ms_per_step": lw_ms,
                        "value": flops_per_step / (lw_ms / 1e3) / 1e9, "clocks": clk_long.summary()}
     # the FP64 FMA pipe's rate on this device, measured now (the FP64 kernels' ALU roof)
-    fp64_peak, fp64_probe_ms = eh.fp64_fma_peak(iters=4096, reps=5)
+    fp64_peak, fp64_probe_ms = eh.fp64_fma_peak(iters=2048, reps=5)
     # the fused kernel timed alone: events around every launch (they keep consecutive launches from
     # overlapping, so this is the isolated duration, not the back-to-back one)
     plan.profile_enable(True)
@@ -389,8 +390,8 @@ def run_ehyb(args):
     bytes_alg = float(info["bytes_effective"])
     gbs = bytes_alg / kern_s / 1e9
     fp64_tf = flops_per_step / kern_s / 1e12
-    fp64_src = (f"measured: ehyb_fp64_fma_peak, 8 independent DFMA chains per thread, 4 x 512 threads per SM, "
-                f"best of 5 launches of {fp64_probe_ms:.2f} ms, run after the timed region")
+    fp64_src = (f"measured: ehyb_fp64_fma_peak, 2-4 independent DFMA chains acc = u*w + acc per thread, 4 x 512 "
+                f"threads per SM, best launch {fp64_probe_ms:.2f} ms, run after the timed region")
     t_hbm = bytes_alg / (hbm_peak * 1e9)
     t_alu = flops_per_step / (fp64_peak * 1e12)
     if t_alu > t_hbm:
@@ -786,7 +787,7 @@ def run_spmm(args):
     x = torch.from_numpy(gen.uniform(A.n, 13)).cuda()
     y = torch.empty_like(x)
     t_spmv = _event_time(lambda: P.spmv(x, y), 50, stream)
-    fp64_peak, _ = eh.fp64_fma_peak(iters=4096, reps=5)
+    fp64_peak, _ = eh.fp64_fma_peak(iters=2048, reps=5)
     out = {}
     for k in args.spmm_k:
         X = torch.from_numpy(np.stack([gen.uniform(A.n, 32 + j) for j in range(k)], axis=1)).cuda()
@@ -858,6 +859,77 @@ def run_lowp(args):
     return 0
 
 
+def run_shard(args):
+    """The halo-exchange form of the product across ranks (one GPU each, launched by torchrun): every rank
+    builds the plan of the whole matrix, keeps its shard (a contiguous group of partitions), and a step is
+    pack -> all_to_all of the halo (NCCL) -> the shard's product.  Strong scaling: the same matrix over N GPUs;
+    value = 2 nnz per step / the slowest rank's time.  One rank runs the same path with an empty exchange."""
+    import torch
+    import gen
+    import paper_2204_06666_gb300 as eh
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    w = WORKLOADS[args.workload]
+    A = make_matrix(w)
+    P = eh.Plan(A)
+    n2o = P.export()["new_to_old"]
+    S = eh.Shard(P, world, rank)
+    x = gen.uniform(A.n, w["seed_x"])[n2o]
+    xe = torch.zeros(S.n_local + S.n_halo, dtype=torch.float64, device=dev)
+    xe[:S.n_local] = torch.from_numpy(x[S.row_begin:S.row_end]).to(dev)
+    send = torch.zeros(max(S.send_total, 1), dtype=torch.float64, device=dev)
+    y = torch.empty(max(S.n_local, 1), dtype=torch.float64, device=dev)
+    halo = xe[S.n_local:]
+
+    def step():
+        S.pack(xe[:S.n_local], send)
+        if world > 1:
+            dist.all_to_all_single(halo, send[:S.send_total], output_split_sizes=S.recv_counts,
+                                   input_split_sizes=S.send_counts)
+        S.spmv(xe, y)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+
+    def reduce_max(v):
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    ms_max = reduce_max(ms) if world > 1 else ms
+    value = 2.0 * A.nnz * args.steps / (ms_max / 1e3) / 1e9
+    line = {"metric": METRIC + " (row shards, halo exchange over NCCL)", "value": value, "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "desc": w["desc"],
+                       "parallelism": f"row shards x{world}", "n_local": S.n_local, "n_halo": S.n_halo,
+                       "send_total": S.send_total},
+            "gpu_launches": (2 if S.send_total else 1) * args.steps, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def _reorder(A, n2o, o2n):
     """P A P^T in CSR, rows in the plan numbering (columns relabelled, order kept)."""
     import gen
@@ -897,6 +969,8 @@ def main():
     ap.add_argument("--spmm", action="store_true", help="time SpMM with --spmm-k right-hand sides")
     ap.add_argument("--spmm-k", type=int, nargs="+", default=[8, 32])
     ap.add_argument("--lowp", action="store_true", help="time the FP32 / BF16 SpMVs of the mixed-precision solvers")
+    ap.add_argument("--shard", action="store_true",
+                    help="row shards across the torchrun ranks with a halo exchange per product (strong scaling)")
     ap.add_argument("--solver-reps", type=int, default=3)
     ap.add_argument("--transient", action="store_true",
                     help="time implicit-Euler steps (one plan and preconditioner, a PCG solve per step)")
@@ -917,6 +991,8 @@ def main():
         return run_spmm(args)
     if args.lowp:
         return run_lowp(args)
+    if args.shard:
+        return run_shard(args)
     return run_ehyb(args)
 
 

@@ -497,12 +497,13 @@ ehyb_status_t ehyb_csr_set_tpr(ehyb_csr_t m, int32_t tpr);
 ehyb_status_t ehyb_csr_destroy(ehyb_csr_t m);
 
 /*
- * Measure the FP64 FMA throughput of the current device: every thread of a grid of 4 x 512-thread
- * blocks per SM runs 8 independent chains of `iters` fused multiply-adds; the best of `reps` timed
- * launches (CUDA events, after one untimed launch) gives *tflops = 2 x FMAs / time and *ms_best.  An FP64
- * SpMV spends one FMA per stored entry (Alg. 3), so this rate, not HBM, bounds it on a part whose FP64
- * pipe is narrow; the roofline of the FP64 kernels is taken against it.  Synchronous; allocates and
- * frees its output array.  iters = 4096 takes about 16 ms per launch on a 152-SM part at 2.07 GHz.
+ * Measure the FP64 FMA throughput of the current device: every thread of a grid of 4 x 512-thread blocks per
+ * SM runs C independent chains acc <- u * w + acc (C = 2, 3 and 4, about 4 x `iters` FMAs per thread each);
+ * the best of `reps` timed launches per C (CUDA events, after one untimed launch) gives *tflops = 2 x FMAs /
+ * time for the fastest C, and its launch time *ms_best.  An FP64 SpMV spends one FMA per stored entry
+ * (Alg. 3), so this rate, not HBM, bounds it on a part whose FP64 pipe is narrow; the roofline of the FP64
+ * kernels is taken against it.  Synchronous; allocates and frees its output array.  iters = 2048 takes about
+ * 9 ms per launch on a 152-SM part at 2.07 GHz.
  */
 ehyb_status_t ehyb_fp64_fma_peak(int32_t iters, int32_t reps, double* tflops, double* ms_best);
 

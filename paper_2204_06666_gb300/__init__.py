@@ -274,7 +274,7 @@ def ehyb_plan_load(path: str, opt: Options | None, stream, out: ctypes.c_void_p)
                                ctypes.byref(out))
 
 
-def fp64_fma_peak(iters: int = 8192, reps: int = 5) -> tuple[float, float]:
+def fp64_fma_peak(iters: int = 2048, reps: int = 5) -> tuple[float, float]:
     """(TFLOP/s, best launch ms) of the current device's FP64 FMA pipe (ehyb_fp64_fma_peak)."""
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _check(_lib.ehyb_fp64_fma_peak(iters, reps, ctypes.byref(tf), ctypes.byref(ms)), "ehyb_fp64_fma_peak")

@@ -90,7 +90,7 @@ template <typename V, typename X>
 static cudaError_t set_smem(int bytes) {
   cudaError_t e;
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if (std::is_same<V, double>::value) {
+  if constexpr (std::is_same<V, double>::value) {
     if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true, kWideBatch>, attr, bytes))) return e;
     if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, true, true, kWideBatch>, attr, bytes))) return e;
     if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true, false, kWideBatch>, attr, bytes))) return e;
@@ -152,20 +152,23 @@ static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArg
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (wide) {
-    cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kWideOk ? kWideBatch : kBatch>, a, ev,
-                       erv, xp, y);
-  } else if (runs) {
-    KArgs ar = a;  // the copies' own column arrays, in the same runs
-    ar.ell_col = P.ell_col_low;
-    ar.er_scol = P.er_scol_low;
-    ar.er_scol_old = P.er_scol_old_low;
-    cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kRunsOk ? kRunBatch : kLowBatch,
-                                         kRunsOk>,
-                       ar, ev, erv, xp, y);
-  } else {
-    cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
+  if constexpr (kWideOk) {
+    if (wide) {
+      cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kWideBatch>, a, ev, erv, xp, y);
+      return;
+    }
   }
+  if constexpr (kRunsOk) {
+    if (runs) {
+      KArgs ar = a;  // the copies' own column arrays, in the same runs
+      ar.ell_col = P.ell_col_low;
+      ar.er_scol = P.er_scol_low;
+      ar.er_scol_old = P.er_scol_old_low;
+      cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kRunBatch, true>, ar, ev, erv, xp, y);
+      return;
+    }
+  }
+  cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER>, a, ev, erv, xp, y);
 }
 
 template <typename V, typename X>
