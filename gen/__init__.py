@@ -290,7 +290,7 @@ def powerlaw_csr(n: int, seed: int, alpha: float, min_len: int = 2, max_len: int
     return CSR(n, np.cumsum(rp), c.astype(np.int32), v, f"powerlaw_n{n}_a{alpha:.2f}")
 
 
-def tuner_matrix(index: int, base_seed: int = 1000, n_min: int = 5000, n_max: int = 100000) -> CSR:
+def tuner_matrix(index: int, base_seed: int = 1000, n_min: int = 5000, n_max: int = 300000) -> CSR:
     """Matrix number `index` of the tuner's data set: even indices are FEM-like (the four element kinds of
     fem_batch), odd ones power-law (alpha ~ U[2, 3]); rows log-uniform in [n_min, n_max]; seed base + index."""
     seed = base_seed + index

@@ -5,7 +5,7 @@
 //              dominance, pattern symmetry, locality of a contiguous-block split).
 //   grid     : the knob configurations the tuner chooses among -- partition rows (VecSize) in {Eq. 1
 //              default, 1024, 2048, 4096, 8192, 16384, the shared-memory maximum} x slab width cap in
-//              {none, p99, p90 of the row lengths} x lanes per row in {1, 2, 4}: 63 configurations.
+//              {none, p99, p90, p75 of the row lengths} x lanes per row in {1, 2, 4, 8}: 112 configurations.
 //   sweep    : builds every configuration (host encodings in parallel threads, one partitioning per
 //              distinct partition size), uploads and times each one's ehyb_spmv on the GPU; the
 //              exhaustive answer, used as training data, as the fallback and as the yardstick of the
@@ -27,8 +27,8 @@
 namespace ehyb {
 namespace {
 
-constexpr int kSlices = 7, kCaps = 3, kTprs = 3, kGrid = kSlices * kCaps * kTprs;
-const int kTprVal[kTprs] = {1, 2, 4};
+constexpr int kSlices = 7, kCaps = 4, kTprs = 4, kGrid = kSlices * kCaps * kTprs;
+const int kTprVal[kTprs] = {1, 2, 4, 8};
 
 double pct(const std::vector<int64_t>& sorted, double q) {
   if (sorted.empty()) return 0.0;
@@ -118,6 +118,7 @@ void grid_values(int64_t n, const int64_t* rp, int sms, int smem_optin, int32_t 
   caps[0] = 0;
   caps[1] = (int32_t)std::max(1.0, pct(len, 0.99));
   caps[2] = (int32_t)std::max(1.0, pct(len, 0.90));
+  caps[3] = (int32_t)std::max(1.0, pct(len, 0.75));
 }
 
 struct TunerModel {
@@ -308,8 +309,8 @@ ehyb_status_t learned_choice(int64_t n, const int64_t* rp, const int32_t* col, c
     const double d = std::fabs(std::log2((double)slices[si]) - (double)out[0]);
     if (d < bd) { bd = d; bs = si; }
   }
-  const int ci = (int)std::min(2.0f, std::max(0.0f, std::round(out[1])));
-  const int ti = (int)std::min(2.0f, std::max(0.0f, std::round(out[2])));
+  const int ci = (int)std::min((float)(kCaps - 1), std::max(0.0f, std::round(out[1])));
+  const int ti = (int)std::min((float)(kTprs - 1), std::max(0.0f, std::round(out[2])));
   *slice_rows = slices[bs];
   *cap = caps[ci];
   *tpr = kTprVal[ti];

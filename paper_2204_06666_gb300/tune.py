@@ -4,8 +4,8 @@
     python -m paper_2204_06666_gb300.tune train --data sweeps_*.npz --out tuner_model.npz
     python -m paper_2204_06666_gb300.tune evaluate --model tuner_model.npz --data heldout.npz
 
-* sweep: matrix i of the data set (gen.tuner_matrix(i): FEM-like for even i, power-law for odd i, 5k-100k
-  rows) is swept over the 63-configuration grid with ehyb_tune_sweep; features (ehyb_features), the grid
+* sweep: matrix i of the data set (gen.tuner_matrix(i): FEM-like for even i, power-law for odd i, 5k-300k
+  rows) is swept over the 112-configuration grid with ehyb_tune_sweep; features (ehyb_features), the grid
   and the measured times are stored.
 * train: targets are the fastest configuration's (log2 VecSize, cap index, log2 lanes, log ns per entry),
   standardised; the 16 -> 64 -> 64 -> 4 network is trained on the GPU by the library's own forward,
@@ -34,7 +34,8 @@ import gen  # noqa: E402
 from . import Mlp, features, tune_sweep, tuner_predict, tuner_set_model  # noqa: E402
 
 MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuner_model.npz")
-CAP_NAMES = ("none", "p99", "p90")
+CAP_NAMES = ("none", "p99", "p90", "p75")
+N_CAPS, N_TPRS = 4, 4   # grid order: VecSize, then cap, then lanes per row
 
 
 def sweep(start: int, count: int, reps: int = 10, log=print) -> dict:
@@ -77,7 +78,7 @@ def targets(d: dict) -> np.ndarray:
     """Per matrix: (log2 VecSize, cap index, log2 lanes, log ns per entry) of the target configuration."""
     best = target_configs(d)
     rows = np.arange(len(best))
-    cap_idx = (best // 3) % 3
+    cap_idx = (best // N_TPRS) % N_CAPS
     ns = d["times"][rows, best] * 1e6 / np.maximum(d["nnz"], 1)
     return np.c_[np.log2(d["slices"][rows, best]), cap_idx, np.log2(d["tprs"][rows, best]), np.log(ns)].astype(
         np.float32)

@@ -83,7 +83,7 @@ def test_mlp_training_on_gpu_reduces_loss(eh):
 def test_sweep_table_and_best(eh):
     A = gen.hex_lap3d(N=24)
     table, best = eh.tune_sweep(A, reps=5)
-    assert len(table) == 63 and all(e["valid"] and e["ms"] > 0 for e in table)
+    assert len(table) == 112 and all(e["valid"] and e["ms"] > 0 for e in table)
     ms = [e["ms"] for e in table]
     assert best == int(np.argmin(ms))
     grid = eh.tune_grid(A)

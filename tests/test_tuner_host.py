@@ -54,14 +54,15 @@ def test_tune_grid_values():
     import paper_2204_06666_gb300 as eh
     A = gen.random_csr(20000, 9, mean_row=10, long_rows=50, long_len=2000)
     g = eh.tune_grid(A)
-    assert len(g) == 63
+    assert len(g) == 112
     K, vec = ef.eq1(A.n, 8, 152, 232448 - 1024 - 32)
     slices = sorted({e["slice_rows"] for e in g})
     assert set(slices) == {vec, 1024, 2048, 4096, 8192, 16384, (232448 - 1024 - 32) // 8 - 2}
     lens = np.sort(np.diff(A.row_ptr))
     caps = {e["ell_width_cap"] for e in g}
-    assert caps == {0, int(lens[int(0.99 * (A.n - 1))]), int(lens[int(0.9 * (A.n - 1))])}
-    assert {e["ell_tpr"] for e in g} == {1, 2, 4}
-    # entry order: VecSize index g // 9, cap index (g // 3) % 3, lanes index g % 3
+    assert caps == {0} | {int(lens[int(q * (A.n - 1))]) for q in (0.99, 0.9, 0.75)}
+    assert {e["ell_tpr"] for e in g} == {1, 2, 4, 8}
+    # entry order: VecSize index g // 16, cap index (g // 4) % 4 (none, p99, p90, p75), lanes index g % 4
     assert g[0]["slice_rows"] == vec and g[0]["ell_width_cap"] == 0 and g[0]["ell_tpr"] == 1
-    assert g[62]["slice_rows"] == (232448 - 1024 - 32) // 8 - 2 and g[62]["ell_tpr"] == 4
+    assert g[4 * 3 + 3]["ell_width_cap"] == int(lens[int(0.75 * (A.n - 1))]) and g[15]["ell_tpr"] == 8
+    assert g[111]["slice_rows"] == (232448 - 1024 - 32) // 8 - 2 and g[111]["ell_tpr"] == 8
