@@ -783,7 +783,7 @@ def run_spmm(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     A = make_matrix(WORKLOADS["hex_elast3d_70"])
-    P = eh.Plan(A)
+    P = eh.Plan(A, slice_rows=args.spmm_slice_rows)   # 0: the Eq. 1 plan of the SpMV
     x = torch.from_numpy(gen.uniform(A.n, 13)).cuda()
     y = torch.empty_like(x)
     t_spmv = _event_time(lambda: P.spmv(x, y), 50, stream)
@@ -800,7 +800,9 @@ def run_spmm(args):
                         "vs_k_spmv": (k * t_spmv) / t}
     line = {"metric": "EHYB SpMM GFLOP/s (FP64, k right-hand sides, 3D hex 70^3)", "unit": "GFLOP/s",
             "value": out[f"k{args.spmm_k[0]}"]["gflops"], "higher_is_better": True, "n_gpus": 1, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "hex_elast3d_70", "n": A.n, "nnz": A.nnz},
+            "data": "synthetic", "config": {"workload": "hex_elast3d_70", "n": A.n, "nnz": A.nnz,
+                                             "slice_rows": P.info()["slice_rows"], "nparts": P.info()["nparts"],
+                                             "er_fraction": P.info()["er_nnz"] / A.nnz},
             "spmv_ms": t_spmv, "fp64_peak_tflops": fp64_peak, "fp64_peak_source": "measured (ehyb_fp64_fma_peak)",
             "spmm": out}
     print(json.dumps(line), flush=True)
@@ -968,6 +970,8 @@ def main():
                     help="shared-memory budget per block of batched plans in bytes (caps partition rows; 0 = device max)")
     ap.add_argument("--spmm", action="store_true", help="time SpMM with --spmm-k right-hand sides")
     ap.add_argument("--spmm-k", type=int, nargs="+", default=[8, 32])
+    ap.add_argument("--spmm-slice-rows", type=int, default=0,
+                    help="VecSize of the SpMM plan (0: Eq. 1, as the SpMV); smaller partitions fit wider column chunks")
     ap.add_argument("--lowp", action="store_true", help="time the FP32 / BF16 SpMVs of the mixed-precision solvers")
     ap.add_argument("--shard", action="store_true",
                     help="row shards across the torchrun ranks with a halo exchange per product (strong scaling)")
