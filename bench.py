@@ -821,12 +821,12 @@ def run_lowp(args):
     w = WORKLOADS[args.workload]
     A = make_matrix(w)
     hbm, hbm_src = measured_peaks()
-    P32 = eh.Plan(A, lowp=1)
+    P32 = eh.Plan(A, lowp=1, lowp_group=args.lowp_group)
     ex = P32.export()
     pv = np.empty(A.n, np.int32)
     for p in range(len(ex["part_ptr"]) - 1):
         pv[ex["new_to_old"][ex["part_ptr"][p]:ex["part_ptr"][p + 1]]] = p
-    P16 = eh.Plan(A, lowp=2, part_vec=pv)
+    P16 = eh.Plan(A, lowp=2, part_vec=pv, lowp_group=args.lowp_group)
     info = P32.info()
     slab, er, n = info["ell_nnz"], info["er_nnz"], A.n
     xh = gen.uniform(A.n, w["seed_x"])
@@ -854,7 +854,8 @@ def run_lowp(args):
     line = {"metric": "EHYB low-precision SpMV effective GB/s (FP32 values, FP32 x/y)", "unit": "GB/s",
             "value": out["f32"]["gbs"], "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "hbm_peak_gbs": hbm,
-                       "hbm_peak_source": hbm_src, "reps": reps},
+                       "hbm_peak_source": hbm_src, "reps": reps, "lowp_group": [P32.info()["lowp_group"],
+                                                                            P16.info()["lowp_group"]]},
             "spmv": out,
             "f32_vs_f64_rel_l2": float(np.linalg.norm(y - ref) / np.linalg.norm(ref))}
     print(json.dumps(line), flush=True)
@@ -973,6 +974,8 @@ def main():
     ap.add_argument("--spmm-slice-rows", type=int, default=0,
                     help="VecSize of the SpMM plan (0: Eq. 1, as the SpMV); smaller partitions fit wider column chunks")
     ap.add_argument("--lowp", action="store_true", help="time the FP32 / BF16 SpMVs of the mixed-precision solvers")
+    ap.add_argument("--lowp-group", type=int, default=0, choices=[0, 1, 4],
+                    help="slot layout of the FP32 / BF16 copies: 0 automatic, 1 column-major, 4 runs of four")
     ap.add_argument("--shard", action="store_true",
                     help="row shards across the torchrun ranks with a halo exchange per product (strong scaling)")
     ap.add_argument("--solver-reps", type=int, default=3)

@@ -1,6 +1,7 @@
 """Parity cases run against the bounds-checked library (EHYB_LIBRARY points at libehyb_checked.so) by
-test_gpu_checked.py: the SpMV in every layout and precision, SpMM, the batched launch, CG, PCG and plan files,
-each followed by a read of the plan status word, which must not report a bounds violation."""
+test_gpu_checked.py: the SpMV in every layout and precision (low-precision copies in both slot layouts), SpMM, the
+batched launch, CG (also flexible), PCG, plan files and row shards, each followed by a read of the status word,
+which must not report a bounds violation."""
 import os
 import sys
 import tempfile
@@ -31,7 +32,8 @@ A = gen.random_csr(3001, 1, mean_row=11, int_values=True, empty_frac=0.05, long_
 x = gen.int_vector(A.n, 101)
 ref = oracle.spmv(A, x)
 for opt in (dict(), dict(ell_tpr=4), dict(ell_tpr=32), dict(ell_width_cap=6), dict(slice_rows=37, block_threads=64),
-            dict(er_layout=1, ell_tpr=2, er_tpr=4), dict(lowp=1), dict(lowp=2)):
+            dict(er_layout=1, ell_tpr=2, er_tpr=4), dict(lowp=1), dict(lowp=2), dict(lowp=1, lowp_group=4),
+            dict(lowp=2, lowp_group=4, ell_tpr=2)):
     P = eh.Plan(A, **opt)
     xd = torch.from_numpy(x).cuda()
     y = torch.empty_like(xd)
@@ -73,6 +75,9 @@ for refine in (0, 3):
     xx = torch.zeros_like(b)
     st, info = P.cg(b, xx, rtol=1e-10, refine=refine)
     assert st == 0, (refine, info)
+xx = torch.zeros_like(b)
+st, info = P.cg(b, xx, rtol=1e-10, refine=5)        # flexible CG, FP32 inner solve
+assert st == 0 and info["flexible"] == 1, info
 M = eh.Fsai(P, T, lowp=1)
 for solve in (P.pcg, P.pcg_refined):
     xx = torch.zeros_like(b)
@@ -88,4 +93,21 @@ with tempfile.TemporaryDirectory() as d:
     Q.spmv(b, y2)
     assert torch.equal(y1, y2)
     ok(Q)
+# row shards: each rank's product on [own rows | halo], the halo filled from the plan-numbering x directly
+Pn = eh.Plan(T)
+n2o = Pn.export()["new_to_old"]
+xp = torch.from_numpy(gen.uniform(T.n, 4)[n2o]).cuda()
+yp = torch.empty_like(xp)
+assert eh.ehyb_spmv_permuted(Pn.handle, xp.data_ptr(), yp.data_ptr(), torch.cuda.current_stream().cuda_stream) == 0
+for r in range(3):
+    S = eh.Shard(Pn, 3, r)
+    L = S.lists()
+    xe = torch.cat([xp[S.row_begin:S.row_end], xp[torch.from_numpy(L["halo_rows"].astype(np.int64)).cuda()]])
+    y = torch.empty(S.n_local, dtype=torch.float64, device="cuda")
+    S.spmv(xe, y)
+    send = torch.empty(max(S.send_total, 1), dtype=torch.float64, device="cuda")
+    S.pack(xe[:S.n_local], send)
+    torch.cuda.synchronize()
+    assert torch.equal(y, yp[S.row_begin:S.row_end])
+    assert S.info()["device_status"] == 0
 print("CHECKED OK")

@@ -62,3 +62,11 @@ def test_fp64_probe_measures_a_plausible_rate():
     assert ms > 0 and 0.3 * nominal < tf < 1.1 * nominal     # at most the nominal rate, well above a stall
     with pytest.raises(eh.EhybError):
         eh.fp64_fma_peak(iters=0)
+
+
+def test_shard_mode_line_on_one_rank():
+    # one rank: the shard is the whole plan, no halo, one launch per step; the same time as the plan's product
+    d = _line("--shard", "--steps", "50", "--warmup", "3")
+    assert d["scaling"] == "strong" and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["config"]["n_halo"] == 0 and d["config"]["n_local"] == d["config"]["n"]
+    assert d["gpu_launches"] == 50 and set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
