@@ -348,8 +348,9 @@ def run_ehyb(args):
             pg.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs) if l2_resident else e0.elapsed_time(e1)
     clocks = clk.summary()
-    # a short requested window (the default driver run asks for 20 steps, about 3 ms) is repeated over a
-    # long one, so the headline's spread can be judged; the headline stays the requested window
+    # a short requested window (20 steps of the hex product are about 3 ms) is repeated over a long one, so
+    # the spread of the requested window's figure can be read beside it; the line's value stays the requested
+    # window's
     long_window = None
     if args.steps < 200 and not l2_resident:
         with ClockSampler(local) as clk_long:
