@@ -515,9 +515,9 @@ typedef struct {
   double ms;                 /* measured ehyb_spmv time (sweep), 0 when not timed */
 } ehyb_tune_entry_t;
 
-/* Number of knob configurations in the tuning grid (63): VecSize in {Eq. 1 default, 1024, 2048, 4096,
- * 8192, 16384, shared-memory maximum} x slab width cap in {none, p99, p90 row length} x lanes {1, 2, 4};
- * entry g has VecSize index g / 9, cap index (g / 3) % 3, lanes index g % 3. */
+/* Number of knob configurations in the tuning grid (112): VecSize in {Eq. 1 default, 1024, 2048, 4096,
+ * 8192, 16384, shared-memory maximum} x slab width cap in {none, p99, p90, p75 row length} x lanes per row in
+ * {1, 2, 4, 8}; entry g has VecSize index g / 16, cap index (g / 4) % 4, lanes index g % 4. */
 int32_t ehyb_tune_grid_size(void);
 
 /* The grid's knob values for this matrix (no GPU use).  table: ehyb_tune_grid_size() entries. */

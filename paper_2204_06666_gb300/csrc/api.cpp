@@ -237,12 +237,12 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
       }
     }
     if (tuner_path == 0) {  // the sweep decides (asked for, or no model loaded)
-      ehyb_tune_entry_t table[64];
+      std::vector<ehyb_tune_entry_t> table((size_t)ehyb_tune_grid_size());
       int32_t best = -1;
       ehyb_plan_t bp = nullptr;
       ehyb_options_t base = opt;
       base.tuner = 0;
-      st = sweep_impl(n, row_ptr, col, val, base, 10, table, &best, &bp, stream);
+      st = sweep_impl(n, row_ptr, col, val, base, 10, table.data(), &best, &bp, stream);
       if (st != EHYB_OK) return st;
       bp->tuner_path = 2;
       bp->ell_width_cap = table[best].ell_width_cap;
@@ -297,14 +297,14 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     if (ns_per_nnz > 2.0 * pred_ns) {
       ehyb_destroy(*out);
       *out = nullptr;
-      ehyb_tune_entry_t table[64];
+      std::vector<ehyb_tune_entry_t> table((size_t)ehyb_tune_grid_size());
       int32_t best = -1;
       ehyb_options_t base = opt;
       base.tuner = 0;
       base.slice_rows = 0;
       base.ell_width_cap = 0;
       base.ell_tpr = 1;
-      st = sweep_impl(n, row_ptr, col, val, base, 10, table, &best, out, stream);
+      st = sweep_impl(n, row_ptr, col, val, base, 10, table.data(), &best, out, stream);
       if (st != EHYB_OK) return st;
       (*out)->tuner_path = 3;
       (*out)->ell_width_cap = table[best].ell_width_cap;
