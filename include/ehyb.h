@@ -106,6 +106,10 @@ typedef struct {
                                 4 = each lane's slots in runs of four (one vector load per run; the copies get
                                 their own column arrays in that layout), 0 = 4 when a slice holds 32 or more
                                 slab + sliced-ER slots per lane on average, else 1.  Results do not depend on it. */
+  int32_t spmm_rhs;          /* right-hand sides the plan is built for (ehyb_spmm): when slice_rows is 0 and this is
+                                above 1, Eq. 1 sizes the partitions for a KC-column slice of X per block (KC the
+                                largest of 8, 4, 2, 1 dividing it: tau = 8 KC bytes per row), so one chunk covers KC
+                                columns; 0 or 1 = the SpMV's tau of 8 bytes.  Results do not depend on it. */
 } ehyb_options_t;
 
 typedef struct ehyb_plan_s* ehyb_plan_t;
@@ -246,7 +250,8 @@ ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t plan, const float* x, float* y, void* s
  * numbering).  The columns run in chunks of KC in {8, 4, 2, 1} (the largest that divides k and whose
  * KC-wide slice of X fits a block's shared memory), one launch per chunk, after one gather of X into a
  * chunk-major workspace (n x k doubles, allocated by the first call).  Column j of Y equals ehyb_spmv of
- * column j of X bit for bit.  Requires the sliced ER layout.  Asynchronous on `stream`.
+ * column j of X bit for bit.  Requires the sliced ER layout.  Asynchronous on `stream`.  A plan built with
+ * opt.spmm_rhs = k has partitions small enough for whole 8-column chunks (one pass over A per 8 columns).
  */
 ehyb_status_t ehyb_spmm(ehyb_plan_t plan, int32_t k, const double* X, double* Y, void* stream);
 

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("part_vec", ctypes.c_void_p), ("wait_timeout_ns", ctypes.c_int64),
                 ("inject_wait_fault", ctypes.c_int32), ("keep_host", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("er_layout", ctypes.c_int32), ("part_nnz", ctypes.c_int32), ("tuner", ctypes.c_int32),
-                ("host_threads", ctypes.c_int32), ("partitioner", ctypes.c_int32), ("lowp_group", ctypes.c_int32)]
+                ("host_threads", ctypes.c_int32), ("partitioner", ctypes.c_int32), ("lowp_group", ctypes.c_int32),
+                ("spmm_rhs", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -198,6 +198,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
     return EHYB_ERR_INVALID_ARG;
   if (opt.er_layout < 0 || opt.er_layout > 1) return EHYB_ERR_INVALID_ARG;
   if (opt.lowp_group != 0 && opt.lowp_group != 1 && opt.lowp_group != 4) return EHYB_ERR_INVALID_ARG;
+  if (opt.spmm_rhs < 0) return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
       opt.part_nnz < 0 || opt.host_threads < 0 || opt.partitioner < 0 || opt.partitioner > 1 ||
       opt.num_sms < 0 || opt.wait_timeout_ns < 0)
@@ -260,7 +261,12 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   PlanParams prm;
   prm.n = n;
   // Eq. 1 / Eq. 2 with tau = 8 (FP64 x slice), keeping 32 bytes of rounding and alignment slack
-  prm.slice_rows = opt.slice_rows > 0 ? opt.slice_rows : eq1_slice_rows(n, 8, d.sms, budget - 32);
+  // Eq. 1's tau: 8 bytes of x per row, or 8 KC for the KC columns of X one SpMM chunk stages per row (a row of
+  // slack per chunk column kept out of the budget)
+  int kc = 1;
+  for (int c : {8, 4, 2})
+    if (opt.spmm_rhs > 1 && opt.spmm_rhs % c == 0) { kc = c; break; }
+  prm.slice_rows = opt.slice_rows > 0 ? opt.slice_rows : eq1_slice_rows(n, 8 * kc, d.sms, budget - 32 - 16 * kc);
   if (opt.slice_rows == 0 && opt.part_nnz > 0 && n > 0) {  // size partitions by work instead
     const int64_t max_rows = std::min<int64_t>(65536, (budget - 32) / 8 - 2);
     const int64_t rows = nnz > 0 ? ((int64_t)opt.part_nnz * n + nnz - 1) / nnz : n;

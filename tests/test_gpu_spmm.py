@@ -29,11 +29,12 @@ def test_spmm_integer_exact(eh, k):
     assert np.array_equal(Yd.cpu().numpy(), oracle.spmm(A, X))
 
 
-@pytest.mark.parametrize("N,k", [(16, 8), (12, 32)])
-def test_spmm_columns_equal_spmv(eh, N, k):
+@pytest.mark.parametrize("N,k,rhs", [(16, 8, 0), (12, 32, 0), (16, 8, 8), (12, 32, 32)])
+def test_spmm_columns_equal_spmv(eh, N, k, rhs):
+    # rhs: a plan built for k right-hand sides (smaller partitions, whole 8-column chunks)
     A = gen.hex_elast3d(N=N)
     X = np.stack([gen.uniform(A.n, 50 + j) for j in range(k)], axis=1)
-    P = eh.Plan(A)
+    P = eh.Plan(A, spmm_rhs=rhs)
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     Yd = torch.empty_like(Xd)
     P.spmm(Xd, Yd)
@@ -54,7 +55,7 @@ def test_spmm_hex70_k8_as_benchmarked(eh):
     A = gen.hex_elast3d()
     k = 8
     X = np.stack([gen.uniform(A.n, 32 + j) for j in range(k)], axis=1)
-    P = eh.Plan(A)
+    P = eh.Plan(A, spmm_rhs=k)
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     Yd = torch.empty_like(Xd)
     P.spmm(Xd, Yd)

@@ -181,3 +181,13 @@ def test_plan_does_not_depend_on_host_threads(which):
         for k in ("new_to_old", "part_ptr", "slice_ptr", "slice_pos", "ell_col", "ell_val", "er_slice_pos", "er_scol",
                   "er_sval", "row_ell_count", "row_er_count"):
             assert np.array_equal(np.asarray(ref[k]), np.asarray(ex[k])), (t, k)
+
+
+@pytest.mark.parametrize("k,kc", [(8, 8), (32, 8), (12, 4), (6, 2), (3, 1)])
+def test_plan_for_k_right_hand_sides_follows_eq1(k, kc):
+    # Eq. 1 with tau = 8 KC bytes per row: a block stages a KC-column slice of X (KC the largest of 8, 4, 2, 1
+    # dividing k), a row of slack per column kept out of the budget
+    A = gen.hex_elast3d(N=30)
+    P = _plan(A, spmm_rhs=k, num_sms=152)
+    K, vec = ef.eq1(A.n, 8 * kc, 152, 232448 - 1024 - 32 - 16 * kc)
+    assert P.info()["slice_rows"] == vec
