@@ -216,6 +216,17 @@ def recorded_traffic(workload: str, layout: str):
     return float(r["dram_bytes_per_launch"]), r.get("note")
 
 
+def _busy(stream, cycles: int = 4_000_000):
+    """Queue about 2 ms of device-side waiting on `stream` before a timed window's start event, so the GPU is
+    still busy while the host enqueues the event and the window's first launches: otherwise an idle stream
+    puts the host's launch latency of the first kernel inside the window.  Nothing of the window's work runs
+    before its start event."""
+    import torch
+    if hasattr(torch.cuda, "_sleep"):
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(cycles)
+
+
 def aggregate(local_ms: float, world: int, units_per_rank: float, reduce_max=None):
     """Whole-job throughput: the max of the ranks' times, all ranks' units.  reduce_max(x) returns the max of
     x over ranks (identity for one rank).  Returns (value in units/s, max ms)."""
@@ -339,6 +350,7 @@ def run_ehyb(args):
                 plan.spmv(xd, yd)
                 evs[i][1].record(stream)
         else:
+            _busy(stream)
             e0.record(stream)
             for _ in range(args.steps):
                 plan.spmv(xd, yd)
@@ -355,6 +367,7 @@ def run_ehyb(args):
     if args.steps < 200 and not l2_resident:
         with ClockSampler(local) as clk_long:
             torch.cuda.synchronize()
+            _busy(stream)
             e0.record(stream)
             for _ in range(LONG_WINDOW_STEPS):
                 plan.spmv(xd, yd)
@@ -905,6 +918,7 @@ def run_shard(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        _busy(stream)
         e0.record(stream)
         for _ in range(args.steps):
             step()
