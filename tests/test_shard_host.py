@@ -153,3 +153,25 @@ def test_gloo_ranks_exchange_and_cg(world, name, port):
     # another summation order separate after about 22 iterations, whatever computes them)
     m = min(20, it)
     assert np.allclose(out[0][6][:m], hist_o[:m], rtol=1e-8)
+
+
+def test_shard_edge_cases():
+    import paper_2204_06666_gb300 as eh
+    # no rows at all: every rank's shard is empty and has nothing to exchange
+    Z = gen.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    P = _plan(Z)
+    for r in range(3):
+        i = eh.Shard(P, 3, r).info()
+        assert i["n_local"] == 0 and i["n_halo"] == 0 and i["send_total"] == 0
+    # one row: rank 0 owns it, the others are empty
+    one = gen.CSR(1, np.array([0, 1], np.int64), np.array([0], np.int32), np.array([2.0]))
+    P = _plan(one)
+    infos = [eh.Shard(P, 4, r).info() for r in range(4)]
+    assert sum(i["n_local"] for i in infos) == 1 and all(i["n_halo"] == 0 for i in infos)
+    # a rank outside [0, nranks) and a plan with CSR-line extra rows are refused
+    A = gen.tet_lap3d(N=6)
+    with pytest.raises(eh.EhybError):
+        eh.Shard(_plan(A), 2, 2)
+    with pytest.raises(eh.EhybError) as e:
+        eh.Shard(_plan(A, er_layout=1), 2, 0)
+    assert e.value.status == 7
