@@ -333,33 +333,44 @@ int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector
   return first_size;
 }
 
+// Per-vertex state of the greedy growth, packed so that visiting a vertex touches one cache line (the
+// growth is bound by the latency of these visits, not by arithmetic).
+struct GrowState {
+  int32_t next, prev;  // links of the gain list the vertex is queued in
+  int32_t key;         // its gain while queued; -1 not queued, -2 done (all its rows assigned)
+  int32_t conn;        // its edges into the part being grown
+  int32_t done_nb;     // its neighbours already done
+  int32_t stamp;       // the last part whose seed search looked at it
+  int64_t next_row;    // its first row not yet assigned
+};
+constexpr int32_t kDone = -2;
+
 // Max-gain queue of free vertices: one FIFO list per gain value, each vertex in at most one list; a
 // vertex whose gain rises moves to the tail of its new list, so among equal gains the one that reached
 // that gain first leaves first.
 struct GainQueue {
-  std::vector<int32_t> head, tail;       // per gain
-  std::vector<int32_t> next, prev, key;  // per vertex; key -1 = not queued
-  std::vector<int32_t> queued;           // vertices queued since the last clear
+  std::vector<int32_t> head, tail;  // per gain
+  std::vector<int32_t> queued;      // vertices queued since the last clear
+  std::vector<GrowState>& st;
   int top = -1;
-  GainQueue(int64_t nv, int nkeys)
-      : head((size_t)nkeys, -1), tail((size_t)nkeys, -1), next((size_t)nv, -1), prev((size_t)nv, -1),
-        key((size_t)nv, -1) {}
+  GainQueue(std::vector<GrowState>& state, int nkeys) : head((size_t)nkeys, -1), tail((size_t)nkeys, -1), st(state) {}
   void unlink(int32_t v) {
-    const int k = key[(size_t)v];
-    if (prev[(size_t)v] >= 0) next[(size_t)prev[(size_t)v]] = next[(size_t)v];
-    else head[(size_t)k] = next[(size_t)v];
-    if (next[(size_t)v] >= 0) prev[(size_t)next[(size_t)v]] = prev[(size_t)v];
-    else tail[(size_t)k] = prev[(size_t)v];
-    key[(size_t)v] = -1;
+    GrowState& s = st[(size_t)v];
+    if (s.prev >= 0) st[(size_t)s.prev].next = s.next;
+    else head[(size_t)s.key] = s.next;
+    if (s.next >= 0) st[(size_t)s.next].prev = s.prev;
+    else tail[(size_t)s.key] = s.prev;
+    s.key = -1;
   }
   // (re)queue v with gain k at the tail of that gain's list
   void raise(int32_t v, int k) {
-    if (key[(size_t)v] >= 0) unlink(v);
+    GrowState& s = st[(size_t)v];
+    if (s.key >= 0) unlink(v);
     else queued.push_back(v);
-    key[(size_t)v] = k;
-    next[(size_t)v] = -1;
-    prev[(size_t)v] = tail[(size_t)k];
-    if (tail[(size_t)k] >= 0) next[(size_t)tail[(size_t)k]] = v;
+    s.key = k;
+    s.next = -1;
+    s.prev = tail[(size_t)k];
+    if (tail[(size_t)k] >= 0) st[(size_t)tail[(size_t)k]].next = v;
     else head[(size_t)k] = v;
     tail[(size_t)k] = v;
     if (k > top) top = k;
@@ -372,11 +383,13 @@ struct GainQueue {
     return true;
   }
   void clear() {
-    for (int32_t v : queued)
-      if (key[(size_t)v] >= 0) {
-        head[(size_t)key[(size_t)v]] = tail[(size_t)key[(size_t)v]] = -1;
-        key[(size_t)v] = -1;
+    for (int32_t v : queued) {
+      GrowState& s = st[(size_t)v];
+      if (s.key >= 0) {
+        head[(size_t)s.key] = tail[(size_t)s.key] = -1;
+        s.key = -1;
       }
+    }
     queued.clear();
     top = -1;
   }
@@ -425,38 +438,38 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
 
   int64_t maxdeg = 0;
   for (int64_t v = 0; v < nv; ++v) maxdeg = std::max(maxdeg, gx[(size_t)v + 1] - gx[(size_t)v]);
-  GainQueue q(nv, (int)maxdeg + 2);
-  std::vector<int32_t> conn((size_t)nv, 0), touched, members, stamp((size_t)nv, -1);
-  std::vector<int64_t> next_row((size_t)nv);  // first unassigned row of each (new) vertex
-  for (int64_t v = 0; v < nv; ++v) next_row[(size_t)v] = first[(size_t)label[(size_t)v]];
-  std::vector<char> done((size_t)nv, 0);
-  std::vector<int32_t> done_nb((size_t)nv, 0);  // assigned neighbours of each vertex, kept up to date
+  std::vector<GrowState> gs((size_t)nv);
+  for (int64_t v = 0; v < nv; ++v) gs[(size_t)v] = GrowState{-1, -1, -1, 0, 0, -1, first[(size_t)label[(size_t)v]]};
+  GainQueue q(gs, (int)maxdeg + 2);
+  std::vector<int32_t> touched, members;
   int64_t cursor = 0, assigned = 0;
   auto next_free = [&]() -> int32_t {
-    while (cursor < nv && done[(size_t)order[(size_t)cursor]]) ++cursor;
+    while (cursor < nv && gs[(size_t)order[(size_t)cursor]].key == kDone) ++cursor;
     return cursor < nv ? order[(size_t)cursor] : -1;
   };
   int32_t p = 0, seed = start;
   while (assigned < n) {
-    if (seed < 0 || done[(size_t)seed]) seed = next_free();
+    if (seed < 0 || gs[(size_t)seed].key == kDone) seed = next_free();
     members.clear();
     int32_t size = 0;
     // take as many of v's remaining rows as the part holds
     auto add = [&](int32_t v) {
-      const int64_t left = first[(size_t)label[(size_t)v] + 1] - next_row[(size_t)v];
+      GrowState& sv = gs[(size_t)v];
+      const int64_t left = first[(size_t)label[(size_t)v] + 1] - sv.next_row;
       const int64_t take = std::min<int64_t>(left, (int64_t)cap - size);
-      for (int64_t k = 0; k < take; ++k) part[(size_t)next_row[(size_t)v]++] = p;
+      for (int64_t k = 0; k < take; ++k) part[(size_t)sv.next_row++] = p;
       size += (int32_t)take;
       assigned += take;
       if (take < left) return;
-      done[(size_t)v] = 1;
+      sv.key = kDone;
       members.push_back(v);
       for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
-        int32_t u = ga[(size_t)e];
-        ++done_nb[(size_t)u];
-        if (done[(size_t)u]) continue;
-        if (conn[(size_t)u] == 0) touched.push_back(u);
-        q.raise(u, ++conn[(size_t)u]);
+        const int32_t u = ga[(size_t)e];
+        GrowState& su = gs[(size_t)u];
+        ++su.done_nb;
+        if (su.key == kDone) continue;
+        if (su.conn == 0) touched.push_back(u);
+        q.raise(u, ++su.conn);
       }
     };
     add(seed);
@@ -466,7 +479,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       if (v < 0) break;
       add(v);
     }
-    for (int32_t u : touched) conn[(size_t)u] = 0;
+    for (int32_t u : touched) gs[(size_t)u].conn = 0;
     touched.clear();
     q.clear();
     // next seed: the free neighbour of this part with the most already-assigned neighbours (a vertex
@@ -476,10 +489,11 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       int64_t best = -1;
       for (int32_t v : members)
         for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
-          int32_t u = ga[(size_t)e];
-          if (done[(size_t)u] || stamp[(size_t)u] == p) continue;
-          stamp[(size_t)u] = p;
-          const int64_t a = done_nb[(size_t)u];
+          const int32_t u = ga[(size_t)e];
+          GrowState& su = gs[(size_t)u];
+          if (su.key == kDone || su.stamp == p) continue;
+          su.stamp = p;
+          const int64_t a = su.done_nb;
           if (a > best) { best = a; seed = u; }
         }
     }
