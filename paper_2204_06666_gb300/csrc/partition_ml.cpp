@@ -724,7 +724,7 @@ int32_t partition_multilevel(int64_t n, const int64_t* rp, const int32_t* col, i
     // renumber in breadth-first order so that neighbours have nearby numbers: every level then walks
     // memory locally (the caller's numbering may be a random permutation)
     std::vector<int32_t> order, inv((size_t)s.nv);
-    bfs_order(s.nv, s.xadj, s.adj, 0, order);
+    bfs_order(s.nv, s.xadj.data(), s.adj.data(), 0, order);
     for (int64_t i = 0; i < s.nv; ++i) inv[(size_t)order[(size_t)i]] = (int32_t)i;
     g.nv = s.nv;
     g.xadj.assign((size_t)g.nv + 1, 0);

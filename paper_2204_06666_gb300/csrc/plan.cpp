@@ -299,8 +299,7 @@ int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, in
 }
 
 // breadth-first order over every component; the first component starts at `s`
-int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int32_t s,
-                         std::vector<int32_t>& order) {
+int64_t bfs_order(int64_t n, const int64_t* xadj, const int32_t* adj, int32_t s, std::vector<int32_t>& order) {
   std::vector<char> seen((size_t)n, 0);
   order.clear();
   order.reserve((size_t)n);
@@ -336,62 +335,58 @@ int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector
 // Per-vertex state of the greedy growth, packed so that visiting a vertex touches one cache line (the
 // growth is bound by the latency of these visits, not by arithmetic).
 struct GrowState {
-  int32_t next, prev;  // links of the gain list the vertex is queued in
-  int32_t key;         // its gain while queued; -1 not queued, -2 done (all its rows assigned)
-  int32_t conn;        // its edges into the part being grown
-  int32_t done_nb;     // its neighbours already done
-  int32_t stamp;       // the last part whose seed search looked at it
-  int64_t next_row;    // its first row not yet assigned
+  int32_t conn;      // its edges into the part being grown (its gain)
+  int32_t done;      // 1 once all its rows are assigned
+  int32_t done_nb;   // its neighbours already done
+  int32_t left;      // its rows not yet assigned
+  int64_t next_row;  // its first row not yet assigned
 };
-constexpr int32_t kDone = -2;
 
-// Max-gain queue of free vertices: one FIFO list per gain value, each vertex in at most one list; a
-// vertex whose gain rises moves to the tail of its new list, so among equal gains the one that reached
-// that gain first leaves first.
+// rows [row, row + count) go to part p (recorded during the growth, written to `part` afterwards)
+struct RowRun {
+  int64_t row;
+  int32_t count, p;
+};
+
+// Max-gain queue of free vertices.  Bucket k lists, in the order they reached it, the vertices whose gain
+// became k while the current part grew; a vertex whose gain rises is appended to the higher bucket and its
+// entry in the lower one goes stale (an entry is live while its vertex is free and its gain still equals
+// the bucket's).  So the queue pops the free vertex of highest gain and, among equal gains, the one that
+// reached that gain first; stale entries are skipped when the read position passes them.  Gains only rise
+// during a part, so a skipped entry never becomes live again.
 struct GainQueue {
-  std::vector<int32_t> head, tail;  // per gain
-  std::vector<int32_t> queued;      // vertices queued since the last clear
-  std::vector<GrowState>& st;
-  int top = -1;
-  GainQueue(std::vector<GrowState>& state, int nkeys) : head((size_t)nkeys, -1), tail((size_t)nkeys, -1), st(state) {}
-  void unlink(int32_t v) {
-    GrowState& s = st[(size_t)v];
-    if (s.prev >= 0) st[(size_t)s.prev].next = s.next;
-    else head[(size_t)s.key] = s.next;
-    if (s.next >= 0) st[(size_t)s.next].prev = s.prev;
-    else tail[(size_t)s.key] = s.prev;
-    s.key = -1;
-  }
-  // (re)queue v with gain k at the tail of that gain's list
+  std::vector<std::vector<int32_t>> bucket;  // per gain, appended in arrival order
+  std::vector<size_t> rd;                    // per gain, the next entry to read
+  const std::vector<GrowState>& st;
+  int top = -1, used = -1;  // highest bucket that may hold live entries; highest bucket written
+  GainQueue(const std::vector<GrowState>& state, int nkeys) : bucket((size_t)nkeys), rd((size_t)nkeys, 0), st(state) {}
+  // v's gain has just become k
   void raise(int32_t v, int k) {
-    GrowState& s = st[(size_t)v];
-    if (s.key >= 0) unlink(v);
-    else queued.push_back(v);
-    s.key = k;
-    s.next = -1;
-    s.prev = tail[(size_t)k];
-    if (tail[(size_t)k] >= 0) st[(size_t)tail[(size_t)k]].next = v;
-    else head[(size_t)k] = v;
-    tail[(size_t)k] = v;
+    bucket[(size_t)k].push_back(v);
     if (k > top) top = k;
+    if (k > used) used = k;
   }
   bool pop(int32_t& v) {
-    while (top >= 0 && head[(size_t)top] < 0) --top;
-    if (top < 0) return false;
-    v = head[(size_t)top];
-    unlink(v);
-    return true;
-  }
-  void clear() {
-    for (int32_t v : queued) {
-      GrowState& s = st[(size_t)v];
-      if (s.key >= 0) {
-        head[(size_t)s.key] = tail[(size_t)s.key] = -1;
-        s.key = -1;
+    for (; top >= 0; --top) {
+      const std::vector<int32_t>& b = bucket[(size_t)top];
+      size_t& r = rd[(size_t)top];
+      while (r < b.size()) {
+        const int32_t u = b[r++];
+        const GrowState& s = st[(size_t)u];
+        if (!s.done && s.conn == top) {
+          v = u;
+          return true;
+        }
       }
     }
-    queued.clear();
-    top = -1;
+    return false;
+  }
+  void clear() {
+    for (int k = 0; k <= used; ++k) {
+      bucket[(size_t)k].clear();
+      rd[(size_t)k] = 0;
+    }
+    top = used = -1;
   }
 };
 
@@ -410,64 +405,76 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
   // is then renumbered in that search's order (neighbours get nearby numbers), so the second search and
   // the growth below walk memory locally; `label` maps the new numbers back.
   std::vector<int32_t> order;
-  int64_t comp0 = bfs_order(nv, gx, ga, 0, order);
+  int64_t comp0 = bfs_order(nv, gx.data(), ga.data(), 0, order);
   std::vector<int32_t> label(order);  // new vertex -> old vertex
+  std::unique_ptr<int32_t[]> adjr;
   {
     std::vector<int32_t> inv((size_t)nv);
-    for (int64_t k = 0; k < nv; ++k) inv[(size_t)label[(size_t)k]] = (int32_t)k;
     std::vector<int64_t> rx((size_t)nv + 1, 0);
-    for (int64_t k = 0; k < nv; ++k) {
-      const int32_t o = label[(size_t)k];
-      rx[(size_t)k + 1] = rx[(size_t)k] + (gx[(size_t)o + 1] - gx[(size_t)o]);
-    }
-    std::vector<int32_t> ra((size_t)rx[(size_t)nv]);
     parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
       for (int64_t k = lo; k < hi; ++k) {
         const int32_t o = label[(size_t)k];
-        int32_t* d = ra.data() + rx[(size_t)k];
+        inv[(size_t)o] = (int32_t)k;
+        rx[(size_t)k + 1] = gx[(size_t)o + 1] - gx[(size_t)o];
+      }
+    });
+    for (int64_t k = 0; k < nv; ++k) rx[(size_t)k + 1] += rx[(size_t)k];
+    // the renumbered lists go to an uninitialised buffer, first touched by the threads that fill it
+    adjr.reset(new int32_t[(size_t)rx[(size_t)nv] + 1]);
+    int32_t* ra = adjr.get();
+    parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {  // in the old order: the old lists stream
+      for (int64_t o = lo; o < hi; ++o) {
+        int32_t* d = ra + rx[(size_t)inv[(size_t)o]];
         int64_t m = 0;
         for (int64_t e = gx[(size_t)o]; e < gx[(size_t)o + 1]; ++e) d[m++] = inv[(size_t)ga[(size_t)e]];
         std::sort(d, d + m);
       }
     });
     gx.swap(rx);
-    ga.swap(ra);
+    std::vector<int32_t>().swap(ga);
   }
+  const int32_t* G = adjr.get();  // adjacency lists of the renumbered graph (offsets gx)
   const int32_t start = (int32_t)(comp0 - 1);  // the search's last vertex of the first component
-  bfs_order(nv, gx, ga, start, order);
+  bfs_order(nv, gx.data(), G, start, order);
 
   int64_t maxdeg = 0;
   for (int64_t v = 0; v < nv; ++v) maxdeg = std::max(maxdeg, gx[(size_t)v + 1] - gx[(size_t)v]);
   std::vector<GrowState> gs((size_t)nv);
-  for (int64_t v = 0; v < nv; ++v) gs[(size_t)v] = GrowState{-1, -1, -1, 0, 0, -1, first[(size_t)label[(size_t)v]]};
+  parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t v = lo; v < hi; ++v) {
+      const int32_t o = label[(size_t)v];
+      gs[(size_t)v] = GrowState{0, 0, 0, (int32_t)(first[(size_t)o + 1] - first[(size_t)o]), first[(size_t)o]};
+    }
+  });
   GainQueue q(gs, (int)maxdeg + 2);
-  std::vector<int32_t> touched, members;
+  std::vector<int32_t> touched;  // vertices whose gain left 0 in the current part, in that order
+  std::vector<RowRun> runs;      // the assignments in the order they are made
+  runs.reserve((size_t)nv);
   int64_t cursor = 0, assigned = 0;
   auto next_free = [&]() -> int32_t {
-    while (cursor < nv && gs[(size_t)order[(size_t)cursor]].key == kDone) ++cursor;
+    while (cursor < nv && gs[(size_t)order[(size_t)cursor]].done) ++cursor;
     return cursor < nv ? order[(size_t)cursor] : -1;
   };
   int32_t p = 0, seed = start;
   while (assigned < n) {
-    if (seed < 0 || gs[(size_t)seed].key == kDone) seed = next_free();
-    members.clear();
+    if (seed < 0 || gs[(size_t)seed].done) seed = next_free();
     int32_t size = 0;
     // take as many of v's remaining rows as the part holds
     auto add = [&](int32_t v) {
       GrowState& sv = gs[(size_t)v];
-      const int64_t left = first[(size_t)label[(size_t)v] + 1] - sv.next_row;
-      const int64_t take = std::min<int64_t>(left, (int64_t)cap - size);
-      for (int64_t k = 0; k < take; ++k) part[(size_t)sv.next_row++] = p;
-      size += (int32_t)take;
+      const int32_t take = std::min(sv.left, cap - size);
+      runs.push_back(RowRun{sv.next_row, take, p});
+      sv.next_row += take;
+      sv.left -= take;
+      size += take;
       assigned += take;
-      if (take < left) return;
-      sv.key = kDone;
-      members.push_back(v);
+      if (sv.left > 0) return;
+      sv.done = 1;
       for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
-        const int32_t u = ga[(size_t)e];
+        const int32_t u = G[(size_t)e];
         GrowState& su = gs[(size_t)u];
         ++su.done_nb;
-        if (su.key == kDone) continue;
+        if (su.done) continue;
         if (su.conn == 0) touched.push_back(u);
         q.raise(u, ++su.conn);
       }
@@ -479,26 +486,30 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       if (v < 0) break;
       add(v);
     }
-    for (int32_t u : touched) gs[(size_t)u].conn = 0;
+    // next seed: the free neighbour of this part with the most already-assigned neighbours (a vertex
+    // split by the full part stays free and joins whichever part reaches it).  The free neighbours are the
+    // touched vertices still free, listed in the order a scan of the part's vertices and their lists first
+    // meets them; the first of the best wins.
+    seed = -1;
+    int32_t best = -1;
+    for (int32_t u : touched) {
+      GrowState& su = gs[(size_t)u];
+      su.conn = 0;
+      if (!su.done && su.done_nb > best) {
+        best = su.done_nb;
+        seed = u;
+      }
+    }
     touched.clear();
     q.clear();
-    // next seed: the free neighbour of this part with the most already-assigned neighbours (a vertex
-    // split by the full part stays free and joins whichever part reaches it)
-    seed = -1;
-    {
-      int64_t best = -1;
-      for (int32_t v : members)
-        for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
-          const int32_t u = ga[(size_t)e];
-          GrowState& su = gs[(size_t)u];
-          if (su.key == kDone || su.stamp == p) continue;
-          su.stamp = p;
-          const int64_t a = su.done_nb;
-          if (a > best) { best = a; seed = u; }
-        }
-    }
     ++p;
   }
+  parallel_for((int64_t)runs.size(), threads, [&](int64_t lo, int64_t hi) {  // the runs' rows are disjoint
+    for (int64_t k = lo; k < hi; ++k) {
+      const RowRun& r = runs[(size_t)k];
+      std::fill(part.data() + r.row, part.data() + r.row + r.count, r.p);
+    }
+  });
   return p;
 }
 

@@ -128,8 +128,7 @@ int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::v
 
 // breadth-first order of every component of (xadj, adj), the first component from `s`; returns the size
 // of the first component
-int64_t bfs_order(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int32_t s,
-                  std::vector<int32_t>& order);
+int64_t bfs_order(int64_t n, const int64_t* xadj, const int32_t* adj, int32_t s, std::vector<int32_t>& order);
 
 // the supervariable graph: vertex v = run v of `first`, an edge wherever two runs' rows are adjacent
 int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& first,
