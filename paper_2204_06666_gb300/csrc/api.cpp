@@ -460,22 +460,23 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
   P->host_kept = P->host_only || opt.keep_host;
   if (!P->host_kept) {  // keep metadata, drop the bulky arrays
     HostPlan& h = P->host;
-    std::vector<uint16_t>().swap(h.ell_col);
-    std::vector<double>().swap(h.ell_val);
-    std::vector<float>().swap(h.ell_val_f32);
-    std::vector<uint16_t>().swap(h.ell_val_bf16);
-    std::vector<int32_t>().swap(h.er_col);
-    std::vector<double>().swap(h.er_val);
-    std::vector<float>().swap(h.er_val_f32);
-    std::vector<uint16_t>().swap(h.er_val_bf16);
-    std::vector<int32_t>().swap(h.er_scol);
-    std::vector<int32_t>().swap(h.er_scol_old);
-    std::vector<double>().swap(h.er_sval);
-    std::vector<float>().swap(h.er_sval_f32);
-    std::vector<uint16_t>().swap(h.er_sval_bf16);
-    std::vector<uint16_t>().swap(h.ell_col_low);
-    std::vector<int32_t>().swap(h.er_scol_low);
-    std::vector<int32_t>().swap(h.er_scol_old_low);
+    auto drop = [](auto& v) { std::decay_t<decltype(v)>().swap(v); };
+    drop(h.ell_col);
+    drop(h.ell_val);
+    drop(h.ell_val_f32);
+    drop(h.ell_val_bf16);
+    drop(h.er_col);
+    drop(h.er_val);
+    drop(h.er_val_f32);
+    drop(h.er_val_bf16);
+    drop(h.er_scol);
+    drop(h.er_scol_old);
+    drop(h.er_sval);
+    drop(h.er_sval_f32);
+    drop(h.er_sval_bf16);
+    drop(h.ell_col_low);
+    drop(h.er_scol_low);
+    drop(h.er_scol_old_low);
     std::vector<int32_t>().swap(h.old_to_new);
   }
   *out = P.release();

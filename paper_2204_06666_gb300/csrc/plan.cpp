@@ -58,51 +58,60 @@ double mean_slice_width(const HostPlan& P) {
   return P.nslices ? slots / (32.0 * (double)P.nslices) : 0.0;
 }
 
-void make_lowp_copies(HostPlan& P, int lowp, int group) {
+void make_lowp_copies(HostPlan& P, int lowp, int group, int threads) {
   if (lowp == 0) return;
   if (group == 0) group = mean_slice_width(P) >= 32.0 ? kSlotGroup : 1;
   if (P.er_layout != 0) group = 1;  // the run loops read the sliced extra-row layout only
   P.lowp_group = group;
+  const int T = planner_threads(threads);
   const size_t stored = P.ell_val.size(), er_nnz = P.er_val.size(), er_stored = P.er_sval.size();
-  // destination of every column-major slot (identity in group 1)
+  // destination of every column-major slot (identity in group 1); each slice's slots map into its own range
   auto regroup = [&](const std::vector<int64_t>& pos, size_t total, std::vector<int64_t>& dst) {
     dst.resize(total);
-    for (int32_t s = 0; s < P.nslices; ++s) {
-      const int64_t base = pos[(size_t)s];
-      const int32_t w = (int32_t)((pos[(size_t)s + 1] - base) / 32);
-      for (int32_t k = 0; k < w; ++k)
-        for (int32_t lane = 0; lane < 32; ++lane)
-          dst[(size_t)(base + 32 * (int64_t)k + lane)] = slot_pos(base, w, k, lane, group);
-    }
+    parallel_for(P.nslices, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t s = lo; s < hi; ++s) {
+        const int64_t base = pos[(size_t)s];
+        const int32_t w = (int32_t)((pos[(size_t)s + 1] - base) / 32);
+        for (int32_t k = 0; k < w; ++k)
+          for (int32_t lane = 0; lane < 32; ++lane)
+            dst[(size_t)(base + 32 * (int64_t)k + lane)] = slot_pos(base, w, k, lane, group);
+      }
+    }, 256);
+  };
+  // every destination is written once: each loop below runs in parallel pieces
+  auto each = [&](size_t count, auto&& f) {
+    parallel_for((int64_t)count, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t k = lo; k < hi; ++k) f((size_t)k);
+    }, 1 << 15);
   };
   std::vector<int64_t> sd, ed;
   if (group != 1) {
     regroup(P.slice_pos, stored, sd);
     if (P.er_layout == 0) regroup(P.er_slice_pos, er_stored, ed);
     P.ell_col_low.resize(stored);
-    for (size_t k = 0; k < stored; ++k) P.ell_col_low[(size_t)sd[k]] = P.ell_col[k];
+    each(stored, [&](size_t k) { P.ell_col_low[(size_t)sd[k]] = P.ell_col[k]; });
     P.er_scol_low.resize(er_stored);
     P.er_scol_old_low.resize(er_stored);
-    for (size_t k = 0; k < er_stored; ++k) {
+    each(er_stored, [&](size_t k) {
       P.er_scol_low[(size_t)ed[k]] = P.er_scol[k];
       P.er_scol_old_low[(size_t)ed[k]] = P.er_scol_old[k];
-    }
+    });
   }
   auto at = [&](const std::vector<int64_t>& d, size_t k) { return d.empty() ? k : (size_t)d[k]; };
   if (lowp == 1) {
     P.ell_val_f32.resize(stored);
     P.er_val_f32.resize(er_nnz);
     P.er_sval_f32.resize(er_stored);
-    for (size_t k = 0; k < stored; ++k) P.ell_val_f32[at(sd, k)] = (float)P.ell_val[k];
-    for (size_t k = 0; k < er_nnz; ++k) P.er_val_f32[k] = (float)P.er_val[k];
-    for (size_t k = 0; k < er_stored; ++k) P.er_sval_f32[at(ed, k)] = (float)P.er_sval[k];
+    each(stored, [&](size_t k) { P.ell_val_f32[at(sd, k)] = (float)P.ell_val[k]; });
+    each(er_nnz, [&](size_t k) { P.er_val_f32[k] = (float)P.er_val[k]; });
+    each(er_stored, [&](size_t k) { P.er_sval_f32[at(ed, k)] = (float)P.er_sval[k]; });
   } else if (lowp == 2) {
     P.ell_val_bf16.resize(stored);
     P.er_val_bf16.resize(er_nnz);
     P.er_sval_bf16.resize(er_stored);
-    for (size_t k = 0; k < stored; ++k) P.ell_val_bf16[at(sd, k)] = f32_to_bf16_rne((float)P.ell_val[k]);
-    for (size_t k = 0; k < er_nnz; ++k) P.er_val_bf16[k] = f32_to_bf16_rne((float)P.er_val[k]);
-    for (size_t k = 0; k < er_stored; ++k) P.er_sval_bf16[at(ed, k)] = f32_to_bf16_rne((float)P.er_sval[k]);
+    each(stored, [&](size_t k) { P.ell_val_bf16[at(sd, k)] = f32_to_bf16_rne((float)P.ell_val[k]); });
+    each(er_nnz, [&](size_t k) { P.er_val_bf16[k] = f32_to_bf16_rne((float)P.er_val[k]); });
+    each(er_stored, [&](size_t k) { P.er_sval_bf16[at(ed, k)] = f32_to_bf16_rne((float)P.er_sval[k]); });
   }
 }
 
@@ -515,6 +524,17 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
 
 // ---------------------------------------------------------------- Alg. 1 + Alg. 2
 
+// sets every element of v to zero, in contiguous pieces on `threads` threads
+template <class V>
+static void zero_parallel(V& v, int threads) {
+  using T = typename V::value_type;
+  if (v.empty()) return;
+  T* d = v.data();
+  parallel_for((int64_t)v.size(), threads, [d](int64_t lo, int64_t hi) {
+    std::memset((void*)(d + lo), 0, (size_t)(hi - lo) * sizeof(T));
+  }, 1 << 16);
+}
+
 int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, const double* val, HostPlan& P) {
   const double t0 = now_ms();
   const int64_t n = prm.n;
@@ -671,13 +691,21 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   const int64_t er_nnz = P.er_ptr[(size_t)ner];
 
   // Alg. 2: place each entry
-  P.ell_col.assign((size_t)stored, 0);
-  P.ell_val.assign((size_t)stored, 0.0);
-  P.er_col.assign((size_t)er_nnz, 0);
-  P.er_val.assign((size_t)er_nnz, 0.0);
-  P.er_scol.assign((size_t)er_stored, 0);
-  P.er_scol_old.assign((size_t)er_stored, 0);
-  P.er_sval.assign((size_t)er_stored, 0.0);
+  // every slot starts at zero (padding slots keep value 0); the arrays are zeroed in parallel pieces
+  P.ell_col.resize((size_t)stored);
+  P.ell_val.resize((size_t)stored);
+  P.er_col.resize((size_t)er_nnz);
+  P.er_val.resize((size_t)er_nnz);
+  P.er_scol.resize((size_t)er_stored);
+  P.er_scol_old.resize((size_t)er_stored);
+  P.er_sval.resize((size_t)er_stored);
+  zero_parallel(P.ell_col, T);
+  zero_parallel(P.ell_val, T);
+  zero_parallel(P.er_col, T);
+  zero_parallel(P.er_val, T);
+  zero_parallel(P.er_scol, T);
+  zero_parallel(P.er_scol_old, T);
+  zero_parallel(P.er_sval, T);
   // padding slots of the sliced ER part point at the first row of their partition (value 0)
   for (int32_t p = 0; p < nparts && P.er_layout == 0; ++p)
     for (int64_t k = P.er_slice_pos[(size_t)P.slice_ptr[(size_t)p]];
@@ -731,7 +759,7 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     ell_part[(size_t)piece.fetch_add(1)] = ell_sum;
   });
   for (int64_t v : ell_part) P.ell_nnz += v;
-  make_lowp_copies(P, prm.lowp, prm.lowp_group);
+  make_lowp_copies(P, prm.lowp, prm.lowp_group, prm.threads);
   P.reorder_ms = now_ms() - t1;
   return 0;
 }

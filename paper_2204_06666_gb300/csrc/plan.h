@@ -3,7 +3,10 @@
 #pragma once
 #include <algorithm>
 #include <cstdint>
+#include <new>
 #include <thread>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 namespace ehyb {
@@ -21,6 +24,31 @@ inline int64_t slot_pos(int64_t base, int32_t w, int32_t k, int32_t lane, int32_
   return k < wg ? base + 32 * kSlotGroup * (int64_t)(k / kSlotGroup) + kSlotGroup * lane + (k % kSlotGroup)
                 : base + 32 * (int64_t)k + lane;
 }
+
+// Allocator of the plan's large host arrays (slab and extra-row slots and their copies): resize() leaves the
+// new elements uninitialised, so that the planner can zero or fill them in parallel (first touch by many
+// threads instead of one serial value-initialisation of hundreds of megabytes).
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  using value_type = T;
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U>&) noexcept {}
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new ((void*)p) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using SlotVec = std::vector<T, UninitAlloc<T>>;
 
 struct PlanParams {
   int64_t n = 0;
@@ -46,32 +74,32 @@ struct HostPlan {
   // ER width, ties by id), so the warps of a block take the long slices first and the block's tail
   // consists of short ones
   std::vector<int32_t> slice_order;
-  std::vector<uint16_t> ell_col;
-  std::vector<double> ell_val;
-  std::vector<float> ell_val_f32;
-  std::vector<uint16_t> ell_val_bf16;
+  SlotVec<uint16_t> ell_col;
+  SlotVec<double> ell_val;
+  SlotVec<float> ell_val_f32;
+  SlotVec<uint16_t> ell_val_bf16;
   std::vector<int32_t> row_ell_count;
   std::vector<int32_t> er_part_ptr, er_row;
   std::vector<int64_t> er_ptr;
-  std::vector<int32_t> er_col;
-  std::vector<double> er_val;
-  std::vector<float> er_val_f32;
-  std::vector<uint16_t> er_val_bf16;
+  SlotVec<int32_t> er_col;
+  SlotVec<double> er_val;
+  SlotVec<float> er_val_f32;
+  SlotVec<uint16_t> er_val_bf16;
   // er_layout 0: the ER entries of slab slice s, column-major like the slab, 32-bit new-numbering
   // columns; slice width = (er_slice_pos[s+1] - er_slice_pos[s]) / 32
   int32_t er_layout = 0;
   std::vector<int64_t> er_slice_pos;
-  std::vector<int32_t> er_scol;
-  std::vector<int32_t> er_scol_old;  // the same columns in the caller's (original) numbering
-  std::vector<double> er_sval;
-  std::vector<float> er_sval_f32;
-  std::vector<uint16_t> er_sval_bf16;
+  SlotVec<int32_t> er_scol;
+  SlotVec<int32_t> er_scol_old;  // the same columns in the caller's (original) numbering
+  SlotVec<double> er_sval;
+  SlotVec<float> er_sval_f32;
+  SlotVec<uint16_t> er_sval_bf16;
   std::vector<int32_t> row_er_count;
   // slot layout of the FP32 / BF16 copies (slot_pos group); with group 4 they come with their own slab and
   // sliced-ER column arrays in that layout (the FP64 arrays stay column-major)
   int32_t lowp_group = 1;
-  std::vector<uint16_t> ell_col_low;
-  std::vector<int32_t> er_scol_low, er_scol_old_low;
+  SlotVec<uint16_t> ell_col_low;
+  SlotVec<int32_t> er_scol_low, er_scol_old_low;
   int64_t er_nnz = 0;
   int64_t ell_nnz = 0;
   int32_t max_part_rows = 0;
@@ -81,8 +109,8 @@ struct HostPlan {
 // FP32 (lowp 1) or BF16 (lowp 2) copies of the FP64 slab and ER values (FP64 -> FP32 -> BF16, round to
 // nearest even at each step); lowp 0 does nothing.  group: their slot layout (1 or 4; 0 = 4 when a slice
 // holds 32 or more slab + sliced-ER slots per lane on average, else 1); with 4 the columns are copied into
-// that layout too.
-void make_lowp_copies(HostPlan& P, int lowp, int group = 0);
+// that layout too.  threads: host threads of the copy loops (0 = the machine's); the copies do not depend on it.
+void make_lowp_copies(HostPlan& P, int lowp, int group = 0, int threads = 0);
 
 // mean slab + sliced-ER slots per lane of a slice
 double mean_slice_width(const HostPlan& P);
