@@ -309,35 +309,43 @@ int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, in
 
 // breadth-first order over every component; the first component starts at `s`
 int64_t bfs_order(int64_t n, const int64_t* xadj, const int32_t* adj, int32_t s, std::vector<int32_t>& order) {
-  std::vector<char> seen((size_t)n, 0);
-  order.clear();
-  order.reserve((size_t)n);
-  int64_t first_size = -1;
+  // visited flags as bits: 2M vertices take 256 KB, which stays in a core's L2
+  std::vector<uint64_t> seen((size_t)(n + 63) / 64, 0);
+  auto test_set = [&](int32_t u) {
+    uint64_t& w = seen[(size_t)u >> 6];
+    const uint64_t b = 1ull << (u & 63);
+    const bool was = (w & b) != 0;
+    w |= b;
+    return was;
+  };
+  order.resize((size_t)n);
+  int32_t* q = order.data();
+  int64_t tail = 0, first_size = -1;
   // the queue is known a few vertices ahead: their offsets, lists and neighbours' flags are prefetched in
   // three stages (on a randomly numbered graph every one of them is a cache miss otherwise)
   auto run = [&](int32_t r) {
-    size_t h = order.size();
-    order.push_back(r);
-    seen[(size_t)r] = 1;
-    while (h < order.size()) {
-      const size_t q = order.size();
-      if (h + 12 < q) __builtin_prefetch(&xadj[(size_t)order[h + 12]]);
-      if (h + 6 < q) __builtin_prefetch(&adj[(size_t)xadj[(size_t)order[h + 6]]]);
-      if (h + 3 < q) {
-        const int32_t w = order[h + 3];
-        for (int64_t e = xadj[(size_t)w]; e < xadj[(size_t)w + 1]; ++e) __builtin_prefetch(&seen[(size_t)adj[(size_t)e]]);
+    int64_t h = tail;
+    q[tail++] = r;
+    test_set(r);
+    while (h < tail) {
+      if (h + 12 < tail) __builtin_prefetch(&xadj[(size_t)q[h + 12]]);
+      if (h + 6 < tail) __builtin_prefetch(&adj[(size_t)xadj[(size_t)q[h + 6]]]);
+      if (h + 3 < tail) {
+        const int32_t w = q[h + 3];
+        for (int64_t e = xadj[(size_t)w]; e < xadj[(size_t)w + 1]; ++e)
+          __builtin_prefetch(&seen[(size_t)adj[(size_t)e] >> 6]);
       }
-      int32_t v = order[h++];
+      const int32_t v = q[h++];
       for (int64_t e = xadj[(size_t)v]; e < xadj[(size_t)v + 1]; ++e) {
-        int32_t u = adj[(size_t)e];
-        if (!seen[(size_t)u]) { seen[(size_t)u] = 1; order.push_back(u); }
+        const int32_t u = adj[(size_t)e];
+        if (!test_set(u)) q[tail++] = u;
       }
     }
   };
-  run(s);
-  first_size = (int64_t)order.size();
+  if (n > 0) run(s);
+  first_size = tail;
   for (int64_t i = 0; i < n; ++i)
-    if (!seen[(size_t)i]) run((int32_t)i);
+    if (!(seen[(size_t)i >> 6] >> (i & 63) & 1)) run((int32_t)i);
   return first_size;
 }
 
