@@ -31,7 +31,7 @@ namespace {
 struct Graph {
   int64_t nv = 0;
   std::vector<int64_t> xadj;
-  std::vector<int32_t> adj;
+  UninitVec<int32_t> adj;
   std::vector<int64_t> ew;    // edge weights, parallel to adj
   std::vector<int64_t> vw;    // vertex weights (rows)
   std::vector<int32_t> orig;  // top-level supervariable of each vertex (finest level of a bisection only)

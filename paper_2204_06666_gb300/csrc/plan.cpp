@@ -128,7 +128,7 @@ int planner_threads(int requested) {
 // duplicate-free.  The rows' own sorted lists are built in parallel; when the pattern is symmetric
 // (every FEM matrix) they already are the answer, otherwise the transpose is merged in.
 void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& xadj,
-                          std::vector<int32_t>& adj) {
+                   UninitVec<int32_t>& adj) {
   std::vector<int64_t> len((size_t)n + 1, 0);
   std::unique_ptr<int32_t[]> tmp(new int32_t[(size_t)(n > 0 ? rp[n] : 0) + 1]);  // every used slot is written
   parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
@@ -205,7 +205,7 @@ void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads
   });
   xadj.assign((size_t)n + 1, 0);
   for (int64_t i = 0; i < n; ++i) xadj[(size_t)i + 1] = xadj[(size_t)i] + ulen[(size_t)i + 1];
-  std::vector<int32_t> out((size_t)xadj[(size_t)n]);
+  UninitVec<int32_t> out((size_t)xadj[(size_t)n]);
   parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
     for (int64_t i = lo; i < hi; ++i)
       std::copy(adj.data() + start[(size_t)i], adj.data() + start[(size_t)i] + ulen[(size_t)i + 1],
@@ -218,7 +218,7 @@ void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads
 // neighbours) coincide -- the dofs of one node of a vector-valued FEM matrix, which are numbered
 // together.  sv_of[i] numbers the runs in row order; run v is rows first[v] .. first[v+1]-1.  Returns
 // the count (n when no two consecutive rows match).
-int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int threads,
+int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const UninitVec<int32_t>& adj, int threads,
                               std::vector<int32_t>& sv_of, std::vector<int64_t>& first) {
   std::vector<uint64_t> key((size_t)n);
   parallel_for(n, threads, [&](int64_t lo, int64_t hi) {
@@ -272,34 +272,45 @@ int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::v
 // rows), an edge wherever two supervariables' rows are adjacent in the pattern of A + A^T; lists sorted.
 // Returns the vertex count.
 int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& first,
-                            std::vector<int64_t>& gx, std::vector<int32_t>& ga) {
+                            std::vector<int64_t>& gx, UninitVec<int32_t>& ga) {
   std::vector<int64_t> xadj;
-  std::vector<int32_t> adj;
+  UninitVec<int32_t> adj;
   sym_adjacency(n, rp, col, threads, xadj, adj);
   std::vector<int32_t> sv_of;
   const int64_t nv = supervariables(n, xadj, adj, threads, sv_of, first);
   if (nv < n) {
-    std::vector<int64_t> glen((size_t)nv + 1, 0);
-    std::vector<std::vector<int32_t>> lists((size_t)nv);
+    // sv_of does not decrease along the rows and every row's list is sorted, so a list mapped through sv_of
+    // is sorted too: its distinct supervariables are found by comparing neighbours, counted in a first pass
+    // and written in a second
+    auto each_neighbour = [&](int64_t v, auto&& f) {
+      const int64_t r = first[(size_t)v];  // the rows of a supervariable share their closed neighbourhood
+      int32_t prev = -1;
+      for (int64_t e = xadj[(size_t)r]; e < xadj[(size_t)r + 1]; ++e) {
+        const int32_t u = sv_of[(size_t)adj[(size_t)e]];
+        if (u != v && u != prev) {
+          f(u);
+          prev = u;
+        }
+      }
+    };
+    gx.assign((size_t)nv + 1, 0);
     parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
       for (int64_t v = lo; v < hi; ++v) {
-        const int64_t r = first[(size_t)v];  // the rows of a supervariable share their closed neighbourhood
-        std::vector<int32_t>& l = lists[(size_t)v];
-        for (int64_t e = xadj[(size_t)r]; e < xadj[(size_t)r + 1]; ++e) {
-          const int32_t u = sv_of[(size_t)adj[(size_t)e]];
-          if (u != v) l.push_back(u);
-        }
-        std::sort(l.begin(), l.end());
-        l.erase(std::unique(l.begin(), l.end()), l.end());
-        glen[(size_t)v + 1] = (int64_t)l.size();
+        int64_t m = 0;
+        each_neighbour(v, [&](int32_t) { ++m; });
+        gx[(size_t)v + 1] = m;
       }
     });
-    gx.assign((size_t)nv + 1, 0);
-    for (int64_t v = 0; v < nv; ++v) gx[(size_t)v + 1] = gx[(size_t)v] + glen[(size_t)v + 1];
+    for (int64_t v = 0; v < nv; ++v) gx[(size_t)v + 1] += gx[(size_t)v];
     ga.resize((size_t)gx[(size_t)nv]);
-    for (int64_t v = 0; v < nv; ++v) std::copy(lists[(size_t)v].begin(), lists[(size_t)v].end(), ga.begin() + gx[(size_t)v]);
+    parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
+      for (int64_t v = lo; v < hi; ++v) {
+        int32_t* d = ga.data() + gx[(size_t)v];
+        each_neighbour(v, [&](int32_t u) { *d++ = u; });
+      }
+    });
     std::vector<int64_t>().swap(xadj);
-    std::vector<int32_t>().swap(adj);
+    UninitVec<int32_t>().swap(adj);
   } else {
     gx.swap(xadj);
     ga.swap(adj);
@@ -353,10 +364,9 @@ int64_t bfs_order(int64_t n, const int64_t* xadj, const int32_t* adj, int32_t s,
 // growth is bound by the latency of these visits, not by arithmetic).
 struct GrowState {
   int32_t conn;      // its edges into the part being grown (its gain)
-  int32_t done;      // 1 once all its rows are assigned
   int32_t done_nb;   // its neighbours already done
-  int32_t left;      // its rows not yet assigned
-  int64_t next_row;  // its first row not yet assigned
+  int32_t left;      // its rows not yet assigned; 0 once it is done
+  int32_t next_row;  // its first row not yet assigned (row counts stay below 2^31)
 };
 
 // rows [row, row + count) go to part p (recorded during the growth, written to `part` afterwards)
@@ -390,13 +400,20 @@ struct GainQueue {
       while (r < b.size()) {
         const int32_t u = b[r++];
         const GrowState& s = st[(size_t)u];
-        if (!s.done && s.conn == top) {
+        if (s.left > 0 && s.conn == top) {
           v = u;
           return true;
         }
       }
     }
     return false;
+  }
+  // the k-th entry after the read position of the top bucket (-1 if none): likely among the next pops
+  int32_t peek(size_t k) const {
+    if (top < 0) return -1;
+    const std::vector<int32_t>& b = bucket[(size_t)top];
+    const size_t i = rd[(size_t)top] + k;
+    return i < b.size() ? b[i] : -1;
   }
   void clear() {
     for (int k = 0; k <= used; ++k) {
@@ -415,7 +432,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
   threads = planner_threads(threads);
   // grow on the supervariable graph: vertex weight = rows of the supervariable
   std::vector<int64_t> first, gx;
-  std::vector<int32_t> ga;
+  UninitVec<int32_t> ga;
   const int64_t nv = supervariable_graph(n, rp, col, threads, first, gx, ga);
 
   // pseudo-peripheral start: the last vertex reached by a breadth-first search from vertex 0.  The graph
@@ -448,7 +465,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       }
     });
     gx.swap(rx);
-    std::vector<int32_t>().swap(ga);
+    UninitVec<int32_t>().swap(ga);
   }
   const int32_t* G = adjr.get();  // adjacency lists of the renumbered graph (offsets gx)
   const int32_t start = (int32_t)(comp0 - 1);  // the search's last vertex of the first component
@@ -460,7 +477,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
   parallel_for(nv, threads, [&](int64_t lo, int64_t hi) {
     for (int64_t v = lo; v < hi; ++v) {
       const int32_t o = label[(size_t)v];
-      gs[(size_t)v] = GrowState{0, 0, 0, (int32_t)(first[(size_t)o + 1] - first[(size_t)o]), first[(size_t)o]};
+      gs[(size_t)v] = GrowState{0, 0, (int32_t)(first[(size_t)o + 1] - first[(size_t)o]), (int32_t)first[(size_t)o]};
     }
   });
   GainQueue q(gs, (int)maxdeg + 2);
@@ -469,12 +486,12 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
   runs.reserve((size_t)nv);
   int64_t cursor = 0, assigned = 0;
   auto next_free = [&]() -> int32_t {
-    while (cursor < nv && gs[(size_t)order[(size_t)cursor]].done) ++cursor;
+    while (cursor < nv && gs[(size_t)order[(size_t)cursor]].left == 0) ++cursor;
     return cursor < nv ? order[(size_t)cursor] : -1;
   };
   int32_t p = 0, seed = start;
   while (assigned < n) {
-    if (seed < 0 || gs[(size_t)seed].done) seed = next_free();
+    if (seed < 0 || gs[(size_t)seed].left == 0) seed = next_free();
     int32_t size = 0;
     // take as many of v's remaining rows as the part holds
     auto add = [&](int32_t v) {
@@ -486,12 +503,11 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       size += take;
       assigned += take;
       if (sv.left > 0) return;
-      sv.done = 1;
       for (int64_t e = gx[(size_t)v]; e < gx[(size_t)v + 1]; ++e) {
         const int32_t u = G[(size_t)e];
         GrowState& su = gs[(size_t)u];
         ++su.done_nb;
-        if (su.done) continue;
+        if (su.left == 0) continue;
         if (su.conn == 0) touched.push_back(u);
         q.raise(u, ++su.conn);
       }
@@ -501,6 +517,17 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
       int32_t v = -1;
       if (!q.pop(v)) v = next_free();  // frontier exhausted: continue this part elsewhere in sweep order
       if (v < 0) break;
+      {  // prefetch for the likely next pops: offsets and state three ahead, the list one ahead, and the
+         // states of the next one's neighbours (hints only; the order of the growth does not depend on them)
+        const int32_t c1 = q.peek(0), c2 = q.peek(1), c3 = q.peek(3);
+        if (c3 >= 0) {
+          __builtin_prefetch(&gx[(size_t)c3]);
+          __builtin_prefetch(&gs[(size_t)c3]);
+        }
+        if (c2 >= 0) __builtin_prefetch(&G[(size_t)gx[(size_t)c2]]);
+        if (c1 >= 0)
+          for (int64_t e = gx[(size_t)c1]; e < gx[(size_t)c1 + 1]; ++e) __builtin_prefetch(&gs[(size_t)G[(size_t)e]]);
+      }
       add(v);
     }
     // next seed: the free neighbour of this part with the most already-assigned neighbours (a vertex
@@ -512,7 +539,7 @@ int32_t partition_graph(int64_t n, const int64_t* rp, const int32_t* col, int32_
     for (int32_t u : touched) {
       GrowState& su = gs[(size_t)u];
       su.conn = 0;
-      if (!su.done && su.done_nb > best) {
+      if (su.left > 0 && su.done_nb > best) {
         best = su.done_nb;
         seed = u;
       }

@@ -25,9 +25,10 @@ inline int64_t slot_pos(int64_t base, int32_t w, int32_t k, int32_t lane, int32_
                 : base + 32 * (int64_t)k + lane;
 }
 
-// Allocator of the plan's large host arrays (slab and extra-row slots and their copies): resize() leaves the
-// new elements uninitialised, so that the planner can zero or fill them in parallel (first touch by many
-// threads instead of one serial value-initialisation of hundreds of megabytes).
+// Allocator of the planner's large host arrays (graph adjacency, slab and extra-row slots and their copies):
+// resize() leaves the new elements uninitialised, so that the planner can zero or fill them in parallel
+// (first touch by many threads instead of one serial value-initialisation of hundreds of megabytes).  Every
+// array of this kind is written in full after each resize.
 template <class T>
 struct UninitAlloc : std::allocator<T> {
   using value_type = T;
@@ -48,7 +49,7 @@ struct UninitAlloc : std::allocator<T> {
   }
 };
 template <class T>
-using SlotVec = std::vector<T, UninitAlloc<T>>;
+using UninitVec = std::vector<T, UninitAlloc<T>>;
 
 struct PlanParams {
   int64_t n = 0;
@@ -74,32 +75,32 @@ struct HostPlan {
   // ER width, ties by id), so the warps of a block take the long slices first and the block's tail
   // consists of short ones
   std::vector<int32_t> slice_order;
-  SlotVec<uint16_t> ell_col;
-  SlotVec<double> ell_val;
-  SlotVec<float> ell_val_f32;
-  SlotVec<uint16_t> ell_val_bf16;
+  UninitVec<uint16_t> ell_col;
+  UninitVec<double> ell_val;
+  UninitVec<float> ell_val_f32;
+  UninitVec<uint16_t> ell_val_bf16;
   std::vector<int32_t> row_ell_count;
   std::vector<int32_t> er_part_ptr, er_row;
   std::vector<int64_t> er_ptr;
-  SlotVec<int32_t> er_col;
-  SlotVec<double> er_val;
-  SlotVec<float> er_val_f32;
-  SlotVec<uint16_t> er_val_bf16;
+  UninitVec<int32_t> er_col;
+  UninitVec<double> er_val;
+  UninitVec<float> er_val_f32;
+  UninitVec<uint16_t> er_val_bf16;
   // er_layout 0: the ER entries of slab slice s, column-major like the slab, 32-bit new-numbering
   // columns; slice width = (er_slice_pos[s+1] - er_slice_pos[s]) / 32
   int32_t er_layout = 0;
   std::vector<int64_t> er_slice_pos;
-  SlotVec<int32_t> er_scol;
-  SlotVec<int32_t> er_scol_old;  // the same columns in the caller's (original) numbering
-  SlotVec<double> er_sval;
-  SlotVec<float> er_sval_f32;
-  SlotVec<uint16_t> er_sval_bf16;
+  UninitVec<int32_t> er_scol;
+  UninitVec<int32_t> er_scol_old;  // the same columns in the caller's (original) numbering
+  UninitVec<double> er_sval;
+  UninitVec<float> er_sval_f32;
+  UninitVec<uint16_t> er_sval_bf16;
   std::vector<int32_t> row_er_count;
   // slot layout of the FP32 / BF16 copies (slot_pos group); with group 4 they come with their own slab and
   // sliced-ER column arrays in that layout (the FP64 arrays stay column-major)
   int32_t lowp_group = 1;
-  SlotVec<uint16_t> ell_col_low;
-  SlotVec<int32_t> er_scol_low, er_scol_old_low;
+  UninitVec<uint16_t> ell_col_low;
+  UninitVec<int32_t> er_scol_low, er_scol_old_low;
   int64_t er_nnz = 0;
   int64_t ell_nnz = 0;
   int32_t max_part_rows = 0;
@@ -147,11 +148,11 @@ inline uint64_t mix64(uint64_t x) {
 
 // pattern of A + A^T without the diagonal, each list sorted and duplicate-free
 void sym_adjacency(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& xadj,
-                   std::vector<int32_t>& adj);
+                   UninitVec<int32_t>& adj);
 
 // supervariables of the graph (xadj, adj): maximal runs of consecutive rows with equal closed
 // neighbourhoods; run v is rows first[v] .. first[v+1]-1, sv_of maps a row to its run
-int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const std::vector<int32_t>& adj, int threads,
+int64_t supervariables(int64_t n, const std::vector<int64_t>& xadj, const UninitVec<int32_t>& adj, int threads,
                        std::vector<int32_t>& sv_of, std::vector<int64_t>& first);
 
 // breadth-first order of every component of (xadj, adj), the first component from `s`; returns the size
@@ -160,7 +161,7 @@ int64_t bfs_order(int64_t n, const int64_t* xadj, const int32_t* adj, int32_t s,
 
 // the supervariable graph: vertex v = run v of `first`, an edge wherever two runs' rows are adjacent
 int64_t supervariable_graph(int64_t n, const int64_t* rp, const int32_t* col, int threads, std::vector<int64_t>& first,
-                            std::vector<int64_t>& gx, std::vector<int32_t>& ga);
+                            std::vector<int64_t>& gx, UninitVec<int32_t>& ga);
 
 // f(lo, hi) on `threads` contiguous pieces of [0, count), in parallel (in the caller when threads <= 1)
 template <typename F>
