@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -107,11 +108,20 @@ ehyb_status_t validate_csr(int64_t nr, int64_t nc, int64_t nnz, const int64_t* r
   if (!rp) return EHYB_ERR_INVALID_ARG;
   if (nnz > 0 && (!col || !val)) return EHYB_ERR_INVALID_ARG;
   if (rp[0] != 0 || rp[nr] != nnz) return EHYB_ERR_INDEX_RANGE;
-  for (int64_t i = 0; i < nr; ++i)
-    if (rp[i + 1] < rp[i]) return EHYB_ERR_INDEX_RANGE;
-  for (int64_t k = 0; k < nnz; ++k)
-    if (col[k] < 0 || (int64_t)col[k] >= nc) return EHYB_ERR_INDEX_RANGE;
-  return EHYB_OK;
+  // both scans run in parallel pieces, each piece folding its violations into one flag (no early exit, so
+  // the compare loops vectorise)
+  std::atomic<int> bad{0};
+  ehyb::parallel_for(nr, ehyb::planner_threads(0), [&](int64_t lo, int64_t hi) {
+    int b = 0;
+    for (int64_t i = lo; i < hi; ++i) b |= rp[i + 1] < rp[i];
+    if (b) bad.store(1);
+  }, 1 << 16);
+  ehyb::parallel_for(nnz, ehyb::planner_threads(0), [&](int64_t lo, int64_t hi) {
+    int b = 0;
+    for (int64_t k = lo; k < hi; ++k) b |= (uint32_t)col[k] >= (uint64_t)nc;
+    if (b) bad.store(1);
+  }, 1 << 18);
+  return bad.load() ? EHYB_ERR_INDEX_RANGE : EHYB_OK;
 }
 
 }  // namespace

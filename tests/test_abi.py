@@ -63,6 +63,25 @@ def test_invalid_inputs_return_codes():
     assert _create(2, 2, rp, col, val, host_only=1) == 0
 
 
+def test_invalid_inputs_found_anywhere_in_large_arrays():
+    # the row-pointer and column scans run in parallel pieces: a single violation at the start, in the
+    # middle or at the end of arrays spanning many pieces is still reported
+    n = 1 << 20
+    rp = np.arange(n + 1, dtype=np.int64) * 2
+    col = np.repeat(np.arange(n, dtype=np.int32), 2)
+    val = np.ones(2 * n)
+    assert _create(n, n, rp, col, val, host_only=1, num_sms=8) == 0
+    for at in (0, n, 2 * n - 1):
+        for bad in (n, -1, 2 ** 31 - 1):
+            c = col.copy()
+            c[at] = bad
+            assert _create(n, n, rp, c, val, host_only=1, num_sms=8) == 3, (at, bad)
+    for at in (1, n // 2, n - 1):
+        r = rp.copy()
+        r[at] = r[at + 1] + 1  # one decrease
+        assert _create(n, n, r, col, val, host_only=1, num_sms=8) == 3, at
+
+
 def test_partition_too_large_for_shared_memory():
     import paper_2204_06666_gb300 as eh
     A = gen.random_csr(40000, 1, mean_row=3)
