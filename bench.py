@@ -309,7 +309,7 @@ def run_ehyb(args):
     x = gen.uniform(A.n, w["seed_x"])
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    plan = eh.Plan(A, partitioner=args.partitioner)
+    plan = eh.Plan(A, partitioner=args.partitioner, er_layout=args.er_layout)
     plan_ms = (time.perf_counter() - t0) * 1e3
     info = plan.info()
     xd = torch.from_numpy(x).to(dev)
@@ -398,7 +398,7 @@ def run_ehyb(args):
     # ---- roofline of the fused kernel.  With the permutation fused (one launch per step) its average
     # duration in the timed region is the step time; otherwise its isolated event-timed duration.
     hbm_peak, peak_src = measured_peaks()
-    fused = info["er_layout"] == 0
+    fused = info["er_layout"] != 1
     kern_iso_s = kern_ms / 1e3 / max(kern_n, 1)
     kern_s = ms_per_step / 1e3 if fused else kern_iso_s
     bytes_alg = float(info["bytes_effective"])
@@ -525,6 +525,7 @@ def run_ehyb(args):
                               f"{FLUSH_BYTES >> 20} MB write that flushes L2 (cold); warm back-to-back steps "
                               f"in 'warm'"),
                        "partitioner": ["greedy growing", "multilevel"][args.partitioner],
+                       "er_layout": info["er_layout"],
                        "nparts": info["nparts"], "slice_rows": info["slice_rows"],
                        "er_fraction": info["er_nnz"] / A.nnz, "er_tpr": info["er_tpr"],
                        "block_threads": info["block_threads"]},
@@ -836,12 +837,12 @@ def run_lowp(args):
     w = WORKLOADS[args.workload]
     A = make_matrix(w)
     hbm, hbm_src = measured_peaks()
-    P32 = eh.Plan(A, lowp=1, lowp_group=args.lowp_group)
+    P32 = eh.Plan(A, lowp=1, lowp_group=args.lowp_group, er_layout=args.er_layout)
     ex = P32.export()
     pv = np.empty(A.n, np.int32)
     for p in range(len(ex["part_ptr"]) - 1):
         pv[ex["new_to_old"][ex["part_ptr"][p]:ex["part_ptr"][p + 1]]] = p
-    P16 = eh.Plan(A, lowp=2, part_vec=pv, lowp_group=args.lowp_group)
+    P16 = eh.Plan(A, lowp=2, part_vec=pv, lowp_group=args.lowp_group, er_layout=args.er_layout)
     info = P32.info()
     slab, er, n = info["ell_nnz"], info["er_nnz"], A.n
     xh = gen.uniform(A.n, w["seed_x"])
@@ -974,6 +975,8 @@ def main():
     ap.add_argument("--impl", default="ehyb", choices=["ehyb", "reference"])
     ap.add_argument("--workload", default="hex_elast3d_70", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-csr", action="store_true")
+    ap.add_argument("--er-layout", type=int, default=0, choices=[0, 1, 2],
+                    help="extra-row layout of the SpMV and --lowp plans (options.er_layout)")
     ap.add_argument("--partitioner", type=int, default=0, choices=[0, 1],
                     help="PartVec of the SpMV plan: 0 greedy graph growing, 1 multilevel")
     ap.add_argument("--plan-io", action="store_true", help="also time saving the plan to a file and loading it")

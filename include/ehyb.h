@@ -88,7 +88,14 @@ typedef struct {
   uint64_t seed;             /* seed of the multilevel partitioner's matching order (partitioner 1); the plan is a
                                 deterministic function of the matrix, the options and this seed */
   int32_t er_layout;         /* extra rows: 0 = sliced with the slab's own slices (one pass per slice, default),
-                                1 = CSR lines, er_tpr lanes each with a shuffle reduction, after a block barrier */
+                                1 = CSR lines, er_tpr lanes each with a shuffle reduction, after a block barrier,
+                                2 = in the slab slices after each row's own entries (slice width = the longest
+                                row of the slice), with 16-bit columns into [the partition's rows | its halo]:
+                                the block stages x at the halo (the distinct columns of its extra entries outside
+                                the partition) after its own slice, so no entry reads x from global memory in the
+                                multiply.  Same results, bit for bit, as layout 0.  EHYB_ERR_TOO_LARGE when a
+                                partition's rows plus halo exceed the shared-memory budget or 65,536; plan files,
+                                ehyb_spmm, batches, FSAI and shards take layout 0 only (EHYB_ERR_UNSUPPORTED) */
   int32_t part_nnz;          /* when slice_rows is 0: size partitions for about this many entries each (capped by
                                 shared memory) instead of Eq. 1's one-per-SM split; for plans run in a batch */
   int32_t tuner;             /* knob choice when slice_rows, ell_width_cap and ell_tpr are 0: 0 = Eq. 1 default,
@@ -133,7 +140,8 @@ typedef struct {
                                 sanity check and the sweep decided */
   int32_t ell_width_cap;     /* slab width cap in force (0 = none) */
   int32_t lowp_group;        /* slot layout of the lowp copies in force (1 or 4; see ehyb_options_t) */
-  int32_t pad;
+  int32_t max_stage_rows;    /* largest rows + halo of a partition (er_layout 2; the largest partition otherwise) */
+  int64_t n_halo;            /* er_layout 2: halo entries over all partitions (0 otherwise) */
 } ehyb_plan_info_t;
 
 /* Pointers into arrays owned by the plan (valid until ehyb_destroy); see ehyb_plan_export. */
@@ -169,6 +177,11 @@ typedef struct {
   const uint16_t* ell_col_low;   /* [ell_stored] */
   const void* er_sval_low;       /* [er_stored] */
   const int32_t* er_scol_low;    /* [er_stored] */
+  /* er_layout 2: partition p's halo is halo_new[halo_ptr[p] .. halo_ptr[p+1]) (plan numbering, ascending); a
+   * slab column c >= part_ptr[p+1] - part_ptr[p] of partition p stands for halo_new[halo_ptr[p] + c - rows] */
+  int64_t n_halo;
+  const int64_t* halo_ptr;       /* [nparts+1] (er_layout 2; all zero otherwise) */
+  const int32_t* halo_new;       /* [n_halo] */
 } ehyb_plan_export_t;
 
 const char* ehyb_status_string(ehyb_status_t s);
@@ -190,13 +203,15 @@ ehyb_status_t ehyb_destroy(ehyb_plan_t plan);
 
 /*
  * y = A x in FP64 (Alg. 3, Sec. 3.2), x and y device arrays of n doubles in the ORIGINAL numbering.
- * With the default sliced ER layout this is ONE launch, one block per partition: the block gathers its
- * slice of x through new_to_old into shared memory (CachedVec), multiplies the slab from shared memory,
- * adds the ER entries of the same slices with x read from global memory through columns in the original
- * numbering, and writes y[new_to_old[r]] directly.  With er_layout 1 a gather kernel first writes
+ * With the default sliced ER layout (and with er_layout 2) this is ONE launch, one block per partition: the
+ * block gathers its slice of x through new_to_old into shared memory (CachedVec), multiplies the slab from
+ * shared memory, adds the ER entries of the same slices with x read from global memory through columns in
+ * the original numbering (er_layout 2: from the halo staged beside the slice), and writes y[new_to_old[r]]
+ * directly.  With er_layout 1 a gather kernel first writes
  * x_p = x[new_to_old] to plan workspace and the ER lines run after the slab.  Effective bytes per call
  * (ehyb_plan_info): 10 per slab entry (value + 16-bit column), 12 per ER entry, 8 n each for x and y,
- * plus 8 per ER line (yIdxER and its CSR offset) with er_layout 1.
+ * plus 8 per ER line (yIdxER and its CSR offset) with er_layout 1.  With er_layout 2 the ER entries cost 10
+ * bytes like the slab's and each halo entry 12 (its column and its x value, read once per partition).
  */
 ehyb_status_t ehyb_spmv(ehyb_plan_t plan, const double* x, double* y, void* stream);
 
@@ -291,8 +306,8 @@ typedef struct {
  *               outer iteration carries the accuracy, so it converges where u_bf16 kappa(A) >= 1 makes
  *               refine 2 / 4 stall; those two hand a stalled solve over to it (info->flexible = 1).
  *               iterations counts inner iterations, refinements the outer steps.
- * Requires the sliced ER layout (er_layout 0).  Returns EHYB_ERR_NOT_CONVERGED (info filled) when the
- * test was not met.  The solver workspace (5 FP64 + 4 FP32 vectors) is allocated on the first call.
+ * Requires er_layout 0 or 2 (every row final after its slice).  Returns EHYB_ERR_NOT_CONVERGED (info
+ * filled) when the test was not met.  The solver workspace (5 FP64 + 4 FP32 vectors) is allocated on the first call.
  */
 ehyb_status_t ehyb_cg(ehyb_plan_t plan, const double* b, double* x, double rtol, int32_t max_iter, int32_t refine,
                       double inner_rtol, ehyb_cg_info_t* info, void* stream);

@@ -80,8 +80,10 @@ def decode(ex: dict, group: int = 1):
 
     ``ex`` holds the exported plan arrays: n, tpr (lanes per row in a slice), new_to_old,
     part_ptr, slice_ptr, slice_pos, ell_col (uint16), ell_val, row_ell_count (per new row), and the
-    extra rows either as CSR lines (er_layout 1: er_row, er_ptr, er_col, er_val) or sliced like the
-    slab (er_layout 0: er_slice_pos, er_scol, er_sval, row_er_count).
+    extra rows either as CSR lines (er_layout 1: er_row, er_ptr, er_col, er_val), sliced like the
+    slab (er_layout 0: er_slice_pos, er_scol, er_sval, row_er_count), or in the slab slices right after
+    each row's own entries (er_layout 2: row_er_count, halo_ptr, halo_new), where a 16-bit column past
+    the partition's rows names entry (column - rows) of the partition's halo list.
     """
     n = int(ex["n"])
     tpr = int(ex["tpr"])
@@ -94,6 +96,13 @@ def decode(ex: dict, group: int = 1):
     ell_val = np.asarray(ex["ell_val"])
     cnt = np.asarray(ex["row_ell_count"], np.int64)
     assert ell_col.dtype == np.uint16
+    layout = int(ex.get("er_layout", 1))
+    if layout == 2:                       # the extra entries follow each row's own in the slab slots
+        extra = np.asarray(ex["row_er_count"], np.int64)
+        halo_ptr = np.asarray(ex["halo_ptr"], np.int64)
+        halo_new = np.asarray(ex["halo_new"], np.int64)
+    else:
+        extra = np.zeros(n, np.int64)
     rows, cols, vals = [], [], []
     for p in range(len(part_ptr) - 1):
         pb, pe = part_ptr[p], part_ptr[p + 1]
@@ -107,16 +116,25 @@ def decode(ex: dict, group: int = 1):
                     continue
                 sub = lane % tpr
                 for k in range(width):
-                    j = k * tpr + sub          # entry j of this row's ELL entries
-                    if j >= cnt[row]:
+                    j = k * tpr + sub          # entry j of this row's slots (its ELL entries, then any extra)
+                    if j >= cnt[row] + extra[row]:
                         continue
                     e = slot_index(pos, width, k, lane, group)
                     local = int(ell_col[e])
-                    assert pb + local < pe, "ELL column outside its partition"
+                    if pb + local < pe:
+                        col = pb + local
+                    else:
+                        assert j >= cnt[row], "ELL column outside its partition"
+                        h = local - (pe - pb)
+                        assert halo_ptr[p] + h < halo_ptr[p + 1], "halo column past the partition's halo"
+                        col = halo_new[halo_ptr[p] + h]
+                        assert not (pb <= col < pe), "halo entry inside its own partition"
                     rows.append(n2o[row])
-                    cols.append(n2o[pb + local])
+                    cols.append(n2o[col])
                     vals.append(ell_val[e])
-    if int(ex.get("er_layout", 1)) == 0:
+    if layout == 2:
+        pass
+    elif layout == 0:
         # extra entries stored in the slab's own slices: same lane -> row map, 32-bit new columns
         er_pos = np.asarray(ex["er_slice_pos"], np.int64)
         er_col = np.asarray(ex["er_scol"], np.int64)

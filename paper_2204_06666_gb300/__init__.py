@@ -59,7 +59,8 @@ class PlanInfo(ctypes.Structure):
                 ("bytes_device", ctypes.c_int64), ("partition_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
                 ("upload_ms", ctypes.c_double), ("device_status", ctypes.c_int32), ("num_sms", ctypes.c_int32),
                 ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64), ("tuner_path", ctypes.c_int32),
-                ("ell_width_cap", ctypes.c_int32), ("lowp_group", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("ell_width_cap", ctypes.c_int32), ("lowp_group", ctypes.c_int32), ("max_stage_rows", ctypes.c_int32),
+                ("n_halo", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,7 +75,8 @@ class PlanExport(ctypes.Structure):
                 ("er_layout", ctypes.c_int32), ("er_stored", ctypes.c_int64), ("er_slice_pos", ctypes.c_void_p),
                 ("er_scol", ctypes.c_void_p), ("er_sval", ctypes.c_void_p), ("row_er_count", ctypes.c_void_p),
                 ("lowp", ctypes.c_int32), ("lowp_group", ctypes.c_int32), ("ell_val_low", ctypes.c_void_p),
-                ("ell_col_low", ctypes.c_void_p), ("er_sval_low", ctypes.c_void_p), ("er_scol_low", ctypes.c_void_p)]
+                ("ell_col_low", ctypes.c_void_p), ("er_sval_low", ctypes.c_void_p), ("er_scol_low", ctypes.c_void_p),
+                ("n_halo", ctypes.c_int64), ("halo_ptr", ctypes.c_void_p), ("halo_new", ctypes.c_void_p)]
 
 
 class CgInfo(ctypes.Structure):
@@ -469,7 +471,8 @@ def _export_dict(ex: PlanExport) -> dict:
             "ell_col_low": arr(ex.ell_col_low, low * ex.ell_stored, np.uint16),
             "er_sval_low": arr(ex.er_sval_low, low * (ex.er_stored if ex.er_layout == 0 else 0),
                                np.float32 if ex.lowp == 1 else np.uint16),
-            "er_scol_low": arr(ex.er_scol_low, low * (ex.er_stored if ex.er_layout == 0 else 0), np.int32)}
+            "er_scol_low": arr(ex.er_scol_low, low * (ex.er_stored if ex.er_layout == 0 else 0), np.int32),
+            "halo_ptr": arr(ex.halo_ptr, nparts + 1, np.int64), "halo_new": arr(ex.halo_new, ex.n_halo, np.int32)}
 
 
 class Shard:

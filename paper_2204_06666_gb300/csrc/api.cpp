@@ -206,7 +206,7 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   if (opt.er_tpr != 0 && !is_pow2_in(opt.er_tpr, 1, 32)) return EHYB_ERR_INVALID_ARG;
   if (opt.block_threads != 0 && (opt.block_threads < 32 || opt.block_threads > 1024 || opt.block_threads % 32))
     return EHYB_ERR_INVALID_ARG;
-  if (opt.er_layout < 0 || opt.er_layout > 1) return EHYB_ERR_INVALID_ARG;
+  if (opt.er_layout < 0 || opt.er_layout > 2) return EHYB_ERR_INVALID_ARG;
   if (opt.lowp_group != 0 && opt.lowp_group != 1 && opt.lowp_group != 4) return EHYB_ERR_INVALID_ARG;
   if (opt.spmm_rhs < 0) return EHYB_ERR_INVALID_ARG;
   if (opt.slice_rows < 0 || opt.ell_width_cap < 0 || opt.lowp < 0 || opt.lowp > 2 || opt.smem_budget < 0 ||
@@ -298,8 +298,10 @@ ehyb_status_t ehyb_plan_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, 
   } catch (const std::bad_alloc&) {
     return EHYB_ERR_OOM;
   }
-  // every partition's slice of x (FP64, plus 16-byte alignment slack) must fit one block's dynamic shared memory
-  if ((int64_t)(H.max_part_rows + 2) * 8 > (int64_t)d.smem_optin - 1024) return EHYB_ERR_TOO_LARGE;
+  // every partition's slice of x (and its halo in er_layout 2; FP64, plus 16-byte alignment slack) must fit
+  // one block's dynamic shared memory
+  if ((int64_t)(std::max(H.max_part_rows, H.max_stage_rows) + 2) * 8 > (int64_t)d.smem_optin - 1024)
+    return EHYB_ERR_TOO_LARGE;
 
   st = plan_finalize(P, opt, d.dev, d.sms, stream, out);
   if (st != EHYB_OK) return st;
@@ -349,7 +351,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
   P->er_rows = 0;
   for (int64_t r = 0; r < n; ++r) P->er_rows += H.row_er_count[(size_t)r] > 0;
   P->er_nnz = H.er_nnz;
-  P->er_stored = H.er_layout == 0 ? (int64_t)H.er_scol.size() : H.er_nnz;
+  P->er_stored = H.er_layout == 0 ? (int64_t)H.er_scol.size() : H.er_layout == 1 ? H.er_nnz : 0;
   P->er_layout = H.er_layout;
   P->nslices = H.nslices;
   if (opt.er_tpr) {
@@ -370,6 +372,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
   D.threads = opt.block_threads;
   D.er_layout = H.er_layout;
   D.max_part_rows = H.max_part_rows;
+  D.max_stage_rows = H.max_stage_rows;
   {  // batch depth: mean slab + sliced-ER slots per lane of a slice (measured: 6 is faster from about 32 up)
     const double w = mean_slice_width(H);
     D.kbatch = (H.er_layout == 0 && w >= 32.0) ? 6 : 8;
@@ -407,6 +410,9 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     const size_t o_ecl = A.add<uint16_t>(H.ell_col_low.size());
     const size_t o_escl = A.add<int32_t>(H.er_scol_low.size());
     const size_t o_esol = A.add<int32_t>(H.er_scol_old_low.size());
+    const size_t o_hp = A.add<int64_t>(H.halo_ptr.size());
+    const size_t o_hn = A.add<int32_t>(H.halo_new.size());
+    const size_t o_ho = A.add<int32_t>(H.halo_old.size());
     const size_t o_xp = A.add<double>((size_t)n + 2);
     const size_t o_xp32 = A.add<float>((size_t)n + 4);
     const size_t o_st = A.add<int32_t>(4);
@@ -426,7 +432,7 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     UP(o_er, H.er_row) UP(o_erp, H.er_ptr) UP(o_erc, H.er_col) UP(o_erv, H.er_val) UP(o_erv32, H.er_val_f32)
     UP(o_erv16, H.er_val_bf16) UP(o_esp, H.er_slice_pos) UP(o_so, H.slice_order) UP(o_esc, H.er_scol) UP(o_eso, H.er_scol_old) UP(o_esv, H.er_sval)
     UP(o_esv32, H.er_sval_f32) UP(o_esv16, H.er_sval_bf16) UP(o_ecl, H.ell_col_low) UP(o_escl, H.er_scol_low)
-    UP(o_esol, H.er_scol_old_low)
+    UP(o_esol, H.er_scol_old_low) UP(o_hp, H.halo_ptr) UP(o_hn, H.halo_new) UP(o_ho, H.halo_old)
 #undef UP
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_st, 0, 16, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_xp, 0, ((size_t)n + 2) * 8, s);
@@ -459,6 +465,9 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
     D.er_sval_f32 = (const float*)(base + o_esv32);
     D.er_sval_bf16 = (const uint16_t*)(base + o_esv16);
     D.status = (int32_t*)(base + o_st);
+    D.halo_ptr = (const int64_t*)(base + o_hp);
+    D.halo_new = (const int32_t*)(base + o_hn);
+    D.halo_old = (const int32_t*)(base + o_ho);
     D.lowp_group = H.lowp_group;
     D.ell_col_low = H.lowp_group == 1 ? D.ell_col : (const uint16_t*)(base + o_ecl);
     D.er_scol_low = H.lowp_group == 1 ? D.er_scol : (const int32_t*)(base + o_escl);
@@ -570,7 +579,7 @@ ehyb_status_t ehyb_spmv(ehyb_plan_t p, const double* x, double* y, void* stream)
   if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   std::pair<cudaEvent_t, cudaEvent_t>* slot;
-  if (p->dev.er_layout == 0) {  // one launch: the permutation of x is fused into the kernel's loads
+  if (p->dev.er_layout != 1) {  // one launch: the permutation of x is fused into the kernel's loads
     if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
     CK(launch_ehyb_f64(p->dev, x, y, 2, s));
     return record_end(slot, s);
@@ -668,7 +677,7 @@ ehyb_status_t ehyb_spmv_lowp(ehyb_plan_t p, const float* x, float* y, void* stre
   if (!x || !y || x == y) return EHYB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   std::pair<cudaEvent_t, cudaEvent_t>* slot;
-  if (p->dev.er_layout == 0) {
+  if (p->dev.er_layout != 1) {
     if ((st = record_begin(p, s, &slot)) != EHYB_OK) return st;
     CK(launch_ehyb_lowp(p->dev, p->lowp, x, y, 2, s));
     return record_end(slot, s);
@@ -707,8 +716,14 @@ ehyb_status_t ehyb_plan_info(ehyb_plan_t p, ehyb_plan_info_t* info) {
   info->ell_stored = p->ell_stored;
   info->er_rows = p->er_rows;
   info->er_nnz = p->er_nnz;
-  // values + column indices + x + y; the CSR layout also reads yIdxER and a line offset per ER line
-  info->bytes_effective = p->ell_nnz * 10 + p->er_nnz * 12 + (p->er_layout == 1 ? p->er_rows * 8 : 0) + H.n * 16;
+  // values + column indices + x + y; the CSR layout also reads yIdxER and a line offset per ER line; the
+  // halo layout reads 16-bit columns for the ER entries and a column and an x value per halo entry
+  const int64_t n_halo = H.halo_ptr.empty() ? 0 : H.halo_ptr.back();
+  info->bytes_effective = p->er_layout == 2
+                              ? p->ell_nnz * 10 + p->er_nnz * 10 + n_halo * 12 + H.n * 16
+                              : p->ell_nnz * 10 + p->er_nnz * 12 + (p->er_layout == 1 ? p->er_rows * 8 : 0) + H.n * 16;
+  info->max_stage_rows = std::max(H.max_part_rows, H.max_stage_rows);
+  info->n_halo = n_halo;
   info->er_layout = p->er_layout;
   info->er_stored = p->er_stored;
   info->tuner_path = p->tuner_path;
@@ -733,12 +748,12 @@ ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
   HostPlan& H = p->host;
   if (!p->host_kept && !p->exported) {  // copy the bulky arrays back from the device
     CK(cudaDeviceSynchronize());
-    const bool sl = p->er_layout == 0;
+    const bool sl = p->er_layout == 0, csr = p->er_layout == 1;
     try {
       H.ell_col.resize((size_t)p->ell_stored);
       H.ell_val.resize((size_t)p->ell_stored);
-      H.er_col.resize(sl ? 0 : (size_t)p->er_nnz);
-      H.er_val.resize(sl ? 0 : (size_t)p->er_nnz);
+      H.er_col.resize(csr ? (size_t)p->er_nnz : 0);
+      H.er_val.resize(csr ? (size_t)p->er_nnz : 0);
       H.er_scol.resize(sl ? (size_t)p->er_stored : 0);
       H.er_sval.resize(sl ? (size_t)p->er_stored : 0);
     } catch (const std::bad_alloc&) {
@@ -784,6 +799,9 @@ ehyb_status_t ehyb_plan_export(ehyb_plan_t p, ehyb_plan_export_t* ex) {
   ex->er_scol = H.er_scol.data();
   ex->er_sval = H.er_sval.data();
   ex->row_er_count = H.row_er_count.data();
+  ex->n_halo = H.halo_ptr.empty() ? 0 : H.halo_ptr.back();
+  ex->halo_ptr = H.halo_ptr.data();
+  ex->halo_new = H.halo_new.data();
   ex->lowp = p->lowp;
   ex->lowp_group = H.lowp_group;
   if (p->host_kept && p->lowp) {

@@ -574,7 +574,7 @@ extern "C" ehyb_status_t ehyb_cg(ehyb_plan_t P, const double* b, double* x, doub
   if (refine < 0 || refine > 6 || !(rtol >= 0.0) || max_iter < 0) return EHYB_ERR_INVALID_ARG;
   const int lowp = refine == 0 ? 0 : (refine % 2 == 1) ? 1 : 2;
   if (refine && P->lowp != lowp) return EHYB_ERR_UNSUPPORTED;  // the plan lacks that value copy
-  if (P->er_layout != 0) return EHYB_ERR_UNSUPPORTED;            // the fused dot needs the sliced ER layout
+  if (P->er_layout == 1) return EHYB_ERR_UNSUPPORTED;            // the fused dot needs every row final after its slice
   const int64_t n = P->dev.n;
   const double t0 = now_s();
   if (n == 0) {

@@ -12,6 +12,7 @@ struct DevPlan {
   int64_t n_x = 0;  // elements of x the extra-row columns index; 0 = n (a shard's x holds its halo too)
   int32_t nparts = 0, tpr = 1, er_tpr = 1, threads = 512;
   int32_t max_part_rows = 0;
+  int32_t max_stage_rows = 0;  // largest rows + halo of a partition: the staged x elements (er_layout 2)
   int32_t kbatch = 8;  // FP64 batch depth (two pipelined half-batches): 6 on wide slices (>= 32 slots a lane), else 8;
                        // the FP32 / BF16 kernels hold 12 (column-major copies) or 16 (copies in 4-slot groups)
   const int32_t* new_to_old = nullptr;
@@ -30,7 +31,10 @@ struct DevPlan {
   const double* er_val = nullptr;
   const float* er_val_f32 = nullptr;
   const uint16_t* er_val_bf16 = nullptr;
-  int32_t er_layout = 0;  // 0: sliced with the slab slices; 1: CSR lines
+  int32_t er_layout = 0;  // 0: sliced with the slab slices; 1: CSR lines; 2: in the slab slices, x staged at a halo
+  const int64_t* halo_ptr = nullptr;  // er_layout 2: partition p's halo is halo_new / halo_old[halo_ptr[p] ..)
+  const int32_t* halo_new = nullptr;
+  const int32_t* halo_old = nullptr;
   const int64_t* er_slice_pos = nullptr;
   const int32_t* er_scol = nullptr;
   const int32_t* er_scol_old = nullptr;  // er_scol in the caller's numbering (x read in place)
@@ -56,7 +60,7 @@ cudaError_t launch_permute_f64(const DevPlan& P, int to_new, const double* in, d
 cudaError_t launch_permute_f32(const DevPlan& P, int to_new, const float* in, float* out, cudaStream_t s);
 
 // Fused slab + ER kernel.  scatter 0: x and y in the plan numbering; 1: x in the plan numbering, y
-// written at new_to_old[r]; 2 (sliced ER layout only, else as 1): x and y both in the caller's numbering,
+// written at new_to_old[r]; 2 (ER layouts 0 and 2, else as 1): x and y both in the caller's numbering,
 // x read through new_to_old while it is staged.  The fused dot product is offered with scatter 0 and 2.
 // Fused dot product sum_r y_r * xp_r in FP64 (sliced ER layout only): one partial per partition in
 // part[nparts]; the last block reduces them in a fixed order into *result and resets *arrive (zero).

@@ -13,14 +13,17 @@
 //        values and columns loaded ahead of their FMAs to keep enough bytes in flight; the FP32 / BF16
 //        copies of plans with wide slices keep each lane's slots in runs of four (slot_pos in
 //        plan.h) and read a run's values and columns with one vector load each;
-//     4. extra-row (ER) entries, two layouts:
+//     4. extra-row (ER) entries, three layouts:
 //        - sliced (er_layout 0, default): the ER entries of the slice's own rows are stored in
 //          the same lane -> row arrangement right behind it (the paper stores its ER part as
 //          stride-32 slices too, Alg. 2); the warp continues with them, gathering x from global
 //          memory, and writes y once -- no block barrier, no read-modify-write, no FP64 shuffle;
 //        - CSR lines (er_layout 1): after a block barrier, er_tpr lanes per ER line with a
-//          shuffle reduction, y[yIdxER] += sum.
-//   In both layouts the rows a block updates are its own, so the paper's second pass over ER
+//          shuffle reduction, y[yIdxER] += sum;
+//        - halo (er_layout 2): step 1 also stages x at the partition's halo (the distinct columns
+//          of its ER entries outside it) behind the slice, and a row's ER entries follow its own
+//          in the slab slots with 16-bit columns into [slice | halo]: step 3 covers them.
+//   In every layout the rows a block updates are its own, so the paper's second pass over ER
 //   slices from a global counter is not needed: no atomics on y, deterministic results.
 #pragma once
 #include <cstdint>
@@ -369,6 +372,9 @@ struct KArgs {
   const int32_t* er_row;
   const int64_t* er_ptr;
   const int32_t* er_col;
+  const int64_t* halo_ptr;  // er_layout 2 (else null): partition p stages x at halo_*[halo_ptr[p] ..) after its rows
+  const int32_t* halo_new;  //   plan numbering
+  const int32_t* halo_old;  //   caller's numbering (GATHER)
   int32_t* status;
   uint64_t timeout_ns;
   int32_t inject;
@@ -454,10 +460,10 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       if (!a.inject) bulk_g2s(xs, xp + a0, bulk_bytes, &bs.bar);
     }
   }
+  const int bd = blockDim.x;
   if (GATHER) {
     // xs[r - a0] = x[new_to_old[r]]: kStage indices, then kStage values in flight per thread (one round
     // covers a partition of kStage * blockDim rows)
-    const int bd = blockDim.x;
     for (int i0 = pb + tid; i0 < pe; i0 += kStage * bd) {
       int c[kStage];
 #pragma unroll
@@ -474,6 +480,26 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     // plain loads: everything when the source is unaligned, else the ragged tail [a1, pe)
     const int lo = bulk_bytes ? (a1 > pb ? a1 : pb) : pb;
     for (int i = lo + tid; i < pe; i += blockDim.x) xs[checked(i - a0, a.smem_elems, a.status)] = xp[i];
+  }
+  // er_layout 2: the halo's x values right after the slice (xs[pe - a0 + j], j < nh), gathered like the
+  // slice itself (plain loads; disjoint from the bulk copy's destination, which ends at a1 - a0).  A loop of
+  // its own: folding it into the gather above slowed the other layouts' staging.
+  int nh = 0;
+  if (a.halo_ptr) {
+    const int64_t h0 = a.halo_ptr[p];
+    nh = (int)(a.halo_ptr[p + 1] - h0);
+    const int32_t* hc = (GATHER ? a.halo_old : a.halo_new) + h0;
+    for (int j0 = tid; j0 < nh; j0 += kStage * bd) {
+      int c[kStage];
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) c[u] = (j0 + u * bd < nh) ? checked(__ldg(hc + j0 + u * bd), a.n, a.status) : -1;
+      X v[kStage];
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) v[u] = c[u] >= 0 ? __ldg(xp + c[u]) : X(0);
+#pragma unroll
+      for (int u = 0; u < kStage; ++u)
+        if (j0 + u * bd < nh) xs[checked(pe - a0 + j0 + u * bd, a.smem_elems, a.status)] = v[u];
+    }
   }
   if (tid == 0) {
     int ok = 1;
@@ -533,12 +559,12 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     }
     X acc;
     if constexpr (RUNS) {  // the copy in runs of four slots (its own column arrays are in a.ell_col / a.er_scol*)
-      acc = slab_dot_runs<V, X, KB>(ell_val + pos, a.ell_col + pos, lane, w, xsl, X(0), pe - pb, a.status);
+      acc = slab_dot_runs<V, X, KB>(ell_val + pos, a.ell_col + pos, lane, w, xsl, X(0), pe - pb + nh, a.status);
       if (ER_SLICED)
         acc = er_dot_runs<V, X>(er_val + epos, (GATHER ? a.er_scol_old : a.er_scol) + epos, lane, we, xp, acc, a.n_x,
                                 a.status);
     } else {
-      acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0), pe - pb, a.status);
+      acc = slab_dot<V, X, KB>(ell_val + pos + lane, a.ell_col + pos + lane, w, xsl, X(0), pe - pb + nh, a.status);
       if (ER_SLICED)
         acc = er_dot<V, X, KB>(er_val + epos + lane, (GATHER ? a.er_scol_old : a.er_scol) + epos + lane, we, xp, acc,
                                a.n_x, a.status);
@@ -630,7 +656,8 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.tpr_log2 = ilog2(P.tpr);
   a.n = P.n;
   a.n_x = P.n_x > 0 ? P.n_x : P.n;
-  a.smem_elems = (int64_t)P.max_part_rows + 2;  // launches set the exact capacity of their shared memory
+  // launches set the exact capacity of their shared memory
+  a.smem_elems = (int64_t)(P.max_stage_rows > P.max_part_rows ? P.max_stage_rows : P.max_part_rows) + 2;
   a.er_tpr_log2 = ilog2(P.er_tpr);
   a.er_slice_pos = P.er_slice_pos;
   a.er_scol = P.er_scol;
@@ -645,6 +672,10 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.er_row = P.er_row;
   a.er_ptr = P.er_ptr;
   a.er_col = P.er_col;
+  const bool halo = P.er_layout == 2;
+  a.halo_ptr = halo ? P.halo_ptr : nullptr;
+  a.halo_new = halo ? P.halo_new : nullptr;
+  a.halo_old = halo ? P.halo_old : nullptr;
   a.status = P.status;
   a.timeout_ns = P.wait_timeout_ns;
   a.inject = P.inject_wait_fault;

@@ -658,8 +658,11 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
     for (int32_t s = P.slice_ptr[(size_t)p]; s < P.slice_ptr[(size_t)p + 1]; ++s) {
       int32_t r0 = pb + (s - P.slice_ptr[(size_t)p]) * rps;
       int32_t r1 = std::min(pe, r0 + rps);
-      int32_t w = 0;
-      for (int32_t r = r0; r < r1; ++r) w = std::max(w, cin[(size_t)P.new_to_old[(size_t)r]]);
+      int32_t w = 0;  // er_layout 2: a row's extra-row slots follow its slab slots in the same slice
+      for (int32_t r = r0; r < r1; ++r) {
+        const int32_t i = P.new_to_old[(size_t)r];
+        w = std::max(w, cin[(size_t)i] + (prm.er_layout == 2 ? cer[(size_t)i] : 0));
+      }
       w = (w + tpr - 1) / tpr;
       P.slice_pos[(size_t)s + 1] = P.slice_pos[(size_t)s] + 32 * (int64_t)w;
     }
@@ -689,12 +692,73 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
   }
   const int64_t er_stored = P.er_slice_pos[(size_t)P.nslices];
 
+  // er_layout 2: each partition's halo, the distinct plan-numbering columns of its rows' extra-row entries
+  // that lie outside the partition, ascending; the kernel stages x at them after the partition's own slice
+  P.halo_ptr.assign((size_t)nparts + 1, 0);
+  P.halo_new.clear();
+  P.halo_old.clear();
+  P.max_stage_rows = P.max_part_rows;
+  if (P.er_layout == 2) {
+    std::vector<std::vector<int32_t>> halo((size_t)nparts);
+    parallel_for(nparts, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t q = lo; q < hi; ++q) {
+        std::vector<int32_t>& h = halo[(size_t)q];
+        for (int32_t r = P.part_ptr[(size_t)q]; r < P.part_ptr[(size_t)q + 1]; ++r) {
+          const int32_t i = P.new_to_old[(size_t)r];
+          for (int64_t k = rp[i]; k < rp[(int64_t)i + 1]; ++k)
+            if (part[(size_t)col[k]] != (int32_t)q) h.push_back(P.old_to_new[(size_t)col[k]]);
+        }
+        std::sort(h.begin(), h.end());
+        h.erase(std::unique(h.begin(), h.end()), h.end());
+      }
+    }, 1);
+    int64_t stage = P.max_part_rows;
+    for (int32_t q = 0; q < nparts; ++q) {
+      P.halo_ptr[(size_t)q + 1] = P.halo_ptr[(size_t)q] + (int64_t)halo[(size_t)q].size();
+      stage = std::max<int64_t>(stage, (int64_t)(P.part_ptr[(size_t)q + 1] - P.part_ptr[(size_t)q]) +
+                                           (int64_t)halo[(size_t)q].size());
+    }
+    if (stage > 65536) return 4;  // the 16-bit local column would overflow
+    P.max_stage_rows = (int32_t)stage;
+    P.halo_new.resize((size_t)P.halo_ptr[(size_t)nparts]);
+    P.halo_old.resize(P.halo_new.size());
+    parallel_for(nparts, T, [&](int64_t lo, int64_t hi) {
+      for (int64_t q = lo; q < hi; ++q) {
+        const std::vector<int32_t>& h = halo[(size_t)q];
+        const int64_t o = P.halo_ptr[(size_t)q];
+        for (size_t t = 0; t < h.size(); ++t) {
+          P.halo_new[(size_t)o + t] = h[t];
+          P.halo_old[(size_t)o + t] = P.new_to_old[(size_t)h[t]];
+        }
+      }
+    }, 1);
+  }
+
   // processing order of the slices inside each partition: longest estimated work first (an ER slot
-  // gathers x from global memory and is counted twice)
+  // gathers x from global memory and is counted twice).  er_layout 2 takes the estimate of layout 0 (slab
+  // and extra widths of the slice taken apart), so both layouts process the slices in the same order and
+  // the solvers' fused dot products, summed in that order, agree bit for bit.
+  std::vector<int64_t> er_work;
+  if (P.er_layout == 2) {
+    er_work.assign((size_t)P.nslices, 0);
+    for (int32_t p = 0; p < nparts; ++p) {
+      const int32_t pb = P.part_ptr[(size_t)p], pe = P.part_ptr[(size_t)p + 1];
+      for (int32_t s = P.slice_ptr[(size_t)p]; s < P.slice_ptr[(size_t)p + 1]; ++s) {
+        const int32_t r0 = pb + (s - P.slice_ptr[(size_t)p]) * rps, r1 = std::min(pe, r0 + rps);
+        int32_t wi = 0, we = 0;
+        for (int32_t r = r0; r < r1; ++r) {
+          wi = std::max(wi, cin[(size_t)P.new_to_old[(size_t)r]]);
+          we = std::max(we, P.row_er_count[(size_t)r]);
+        }
+        er_work[(size_t)s] = 32 * (int64_t)((wi + tpr - 1) / tpr) + 2 * 32 * (int64_t)((we + tpr - 1) / tpr);
+      }
+    }
+  }
   P.slice_order.resize((size_t)P.nslices);
   for (int32_t p = 0; p < nparts; ++p) {
     const int32_t s0 = P.slice_ptr[(size_t)p], s1 = P.slice_ptr[(size_t)p + 1];
     auto work = [&](int32_t s) {
+      if (!er_work.empty()) return er_work[(size_t)s];
       return (P.slice_pos[(size_t)s + 1] - P.slice_pos[(size_t)s]) +
              2 * (P.er_slice_pos[(size_t)s + 1] - P.er_slice_pos[(size_t)s]);
     };
@@ -776,6 +840,19 @@ int build_plan(const PlanParams& prm, const int64_t* rp, const int32_t* col, con
           P.ell_col[(size_t)pos] = (uint16_t)(P.old_to_new[(size_t)c] - pb);
           P.ell_val[(size_t)pos] = val[k];
           ++j;
+        } else if (P.er_layout == 2) {  // after the row's slab slots; column into [own slice | halo]
+          const int32_t cn = P.old_to_new[(size_t)c];
+          int32_t local = cn - pb;
+          if (part[(size_t)c] != p) {
+            const int32_t* h0 = P.halo_new.data() + P.halo_ptr[(size_t)p];
+            const int32_t* h1 = P.halo_new.data() + P.halo_ptr[(size_t)p + 1];
+            local = (P.part_ptr[(size_t)p + 1] - pb) + (int32_t)(std::lower_bound(h0, h1, cn) - h0);
+          }
+          const int64_t jj = cin[(size_t)i] + je;
+          const int64_t pos = base + 32 * (jj / tpr) + lane0 + (int32_t)(jj % tpr);
+          P.ell_col[(size_t)pos] = (uint16_t)local;
+          P.ell_val[(size_t)pos] = val[k];
+          ++je;
         } else if (P.er_layout == 0) {
           const int64_t pos = ebase + 32 * (je / tpr) + lane0 + (int32_t)(je % tpr);
           P.er_scol[(size_t)pos] = P.old_to_new[(size_t)c];

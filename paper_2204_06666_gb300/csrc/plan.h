@@ -58,7 +58,8 @@ struct PlanParams {
   int32_t ell_tpr = 1;        // lanes per row in a slab slice
   int32_t lowp = 0;           // 0 none, 1 fp32, 2 bf16 value copies
   int32_t lowp_group = 0;     // slot layout of the value copies: 1, 4, or 0 = 4 on wide slices (make_lowp_copies)
-  int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR
+  int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR; 2: in the slab
+                              //    slices after each row's own entries, x staged at the partition's halo
   const int32_t* part_vec = nullptr;
   int32_t threads = 0;        // host threads for the parallel phases (0 = the machine's); results do not depend on it
   int32_t partitioner = 0;    // 0 greedy graph growing, 1 multilevel recursive bisection
@@ -96,6 +97,13 @@ struct HostPlan {
   UninitVec<float> er_sval_f32;
   UninitVec<uint16_t> er_sval_bf16;
   std::vector<int32_t> row_er_count;
+  // er_layout 2: no separate extra-row arrays; a row's extra-row entries take the slab slots after its own
+  // (slice width = the longest row of the slice, slab + extra), their 16-bit columns pointing into
+  // [the partition's rows | its halo].  halo_new[halo_ptr[p] .. halo_ptr[p+1]) is partition p's halo in the
+  // plan numbering (ascending), halo_old the same columns in the caller's numbering.
+  std::vector<int64_t> halo_ptr;
+  std::vector<int32_t> halo_new, halo_old;
+  int32_t max_stage_rows = 0;  // largest rows + halo of a partition (= max_part_rows without a halo)
   // slot layout of the FP32 / BF16 copies (slot_pos group); with group 4 they come with their own slab and
   // sliced-ER column arrays in that layout (the FP64 arrays stay column-major)
   int32_t lowp_group = 1;

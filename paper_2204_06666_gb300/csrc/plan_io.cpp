@@ -238,6 +238,7 @@ using namespace ehyb;
 
 extern "C" ehyb_status_t ehyb_plan_save(ehyb_plan_t p, const char* path) {
   if (!p || !path) return EHYB_ERR_INVALID_ARG;
+  if (p->er_layout == 2) return EHYB_ERR_UNSUPPORTED;  // the file holds no halo
   // a copy of the metadata plus the bulky arrays (from the host copy when kept, else from the device)
   HostPlan tmp;
   const HostPlan* src = &p->host;

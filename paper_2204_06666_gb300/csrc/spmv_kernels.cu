@@ -79,7 +79,8 @@ int grid_for(int64_t n, int threads) {
 
 size_t ehyb_smem_bytes(const DevPlan& P, int elem_bytes) {
   const int epv = 16 / elem_bytes;
-  size_t b = (size_t)(P.max_part_rows + epv) * (size_t)elem_bytes;
+  const int32_t rows = P.max_stage_rows > P.max_part_rows ? P.max_stage_rows : P.max_part_rows;
+  size_t b = (size_t)(rows + epv) * (size_t)elem_bytes;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -183,7 +184,7 @@ static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const 
     a.dot_self = dot->self;
   }
   a.skip = skip;
-  const bool sl = P.er_layout == 0;
+  const bool sl = P.er_layout != 1;  // 2: no extra-row slots of its own (zero widths), the sliced kernels run
   const V* erv = sl ? erv_sl : erv_csr;
   if (dot && scatter == 2 && sl) {  // caller's numbering with the fused dot (preconditioner SpMVs)
     launch_pdl<V, X, true, true, true, true>(P, smem, s, a, ev, erv, xp, y);

@@ -1,7 +1,7 @@
 """Parity cases run against the bounds-checked library (EHYB_LIBRARY points at libehyb_checked.so) by
-test_gpu_checked.py: the SpMV in every layout and precision (low-precision copies in both slot layouts), SpMM, the
-batched launch, CG (also flexible), PCG, plan files and row shards, each followed by a read of the status word,
-which must not report a bounds violation."""
+test_gpu_checked.py: the SpMV in every layout (the halo layout included) and precision (low-precision copies in
+both slot layouts), SpMM, the batched launch, CG (also flexible), PCG, plan files and row shards, each followed by
+a read of the status word, which must not report a bounds violation."""
 import os
 import sys
 import tempfile
@@ -33,7 +33,8 @@ x = gen.int_vector(A.n, 101)
 ref = oracle.spmv(A, x)
 for opt in (dict(), dict(ell_tpr=4), dict(ell_tpr=32), dict(ell_width_cap=6), dict(slice_rows=37, block_threads=64),
             dict(er_layout=1, ell_tpr=2, er_tpr=4), dict(lowp=1), dict(lowp=2), dict(lowp=1, lowp_group=4),
-            dict(lowp=2, lowp_group=4, ell_tpr=2)):
+            dict(lowp=2, lowp_group=4, ell_tpr=2), dict(er_layout=2, lowp=1), dict(er_layout=2, lowp=2, ell_tpr=4),
+            dict(er_layout=2, slice_rows=37, block_threads=64)):
     P = eh.Plan(A, **opt)
     xd = torch.from_numpy(x).cuda()
     y = torch.empty_like(xd)
@@ -69,6 +70,13 @@ for M, v, w, Q in zip(mats, xs, ys, plans):
     ok(Q)
 
 T = gen.tet_lap3d(N=12)
+for lay in (2,):  # the halo layout inside the FP64 CG (plan numbering, fused dot)
+    Ph = eh.Plan(T, er_layout=lay)
+    bh = torch.from_numpy(oracle.spmv(T, gen.uniform(T.n, 9))).cuda()
+    xh = torch.zeros_like(bh)
+    st, info = Ph.cg(bh, xh, rtol=1e-10)
+    assert st == 0, info
+    ok(Ph)
 P = eh.Plan(T, lowp=1)
 b = torch.from_numpy(oracle.spmv(T, gen.uniform(T.n, 9))).cuda()
 for refine in (0, 3):

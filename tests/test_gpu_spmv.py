@@ -50,7 +50,9 @@ OPTS = [dict(), dict(ell_tpr=2), dict(ell_tpr=4), dict(ell_tpr=32), dict(ell_wid
         dict(slice_rows=33, block_threads=32),
         dict(er_layout=1, ell_tpr=2, er_tpr=1), dict(er_layout=1, ell_tpr=4, er_tpr=32),
         dict(er_layout=1, ell_tpr=32, er_tpr=8), dict(er_layout=1, ell_width_cap=6, er_tpr=4),
-        dict(er_layout=1, slice_rows=37, block_threads=64)]
+        dict(er_layout=1, slice_rows=37, block_threads=64),
+        dict(er_layout=2), dict(er_layout=2, ell_tpr=4), dict(er_layout=2, ell_width_cap=6, slice_rows=300),
+        dict(er_layout=2, slice_rows=1), dict(er_layout=2, slice_rows=33, block_threads=32)]
 
 
 @pytest.mark.parametrize("opt", OPTS)
@@ -63,7 +65,7 @@ def test_integer_bit_exact_ragged(eh, opt, seed):
     assert np.array_equal(y, oracle.spmv(A, x))
 
 
-@pytest.mark.parametrize("er_layout", [0, 1])
+@pytest.mark.parametrize("er_layout", [0, 1, 2])
 @pytest.mark.parametrize("name,N,slice_rows", [("fem2d", 200, 0), ("hex", 16, 0), ("hex", 16, 700),
                                                ("tet", 20, 0), ("tet", 20, 1000)])
 def test_fem_parity(eh, name, N, slice_rows, er_layout):
@@ -96,6 +98,74 @@ def test_tet126_full_size(eh):
     x = gen.uniform(A.n, 23)
     _, y = _run(eh, A, x)
     _check_fp(A, x, y)
+    # the halo layout: the extra entries after each row's own in the slab slices, x staged at the halo; every
+    # row summed in the same slot order, so the same bits
+    P2, y2 = _run(eh, A, x, er_layout=2)
+    assert P2.info()["er_layout"] == 2 and P2.info()["n_halo"] > 0
+    assert np.array_equal(y2, y)
+
+
+@pytest.mark.parametrize("make", [lambda: gen.tet_lap3d(N=30), lambda: gen.hex_elast3d(N=16),
+                                  lambda: gen.fem2d_p1(N=150),
+                                  lambda: gen.random_csr(5000, 3, mean_row=12, empty_frac=0.05, long_rows=4,
+                                                         long_len=1200, duplicates=True)],
+                         ids=["tet", "hex", "fem2d", "ragged"])
+@pytest.mark.parametrize("slice_rows", [0, 500])
+def test_halo_layout_bit_identical_to_sliced(eh, make, slice_rows):
+    # er_layout 2 against er_layout 0 on the same partition: the fused-permutation entry, the plan-numbering
+    # entry, the allocation-free entry and the FP32 / BF16 products give the same bits
+    A = make()
+    x = gen.uniform(A.n, 31)
+    out = {}
+    for lay in (0, 2):
+        P = eh.Plan(A, slice_rows=slice_rows, er_layout=lay, lowp=1)
+        P16 = eh.Plan(A, slice_rows=slice_rows, er_layout=lay, lowp=2)
+        xd = torch.from_numpy(x).cuda()
+        y = torch.full_like(xd, np.nan)
+        P.spmv(xd, y)
+        xp, yp = torch.empty_like(xd), torch.full_like(xd, np.nan)
+        P.permute(True, xd, xp)
+        P.spmv_permuted(xp, yp)
+        yn = torch.full_like(xd, np.nan)
+        P.spmv_noalloc(xd, yn)
+        x32 = xd.float()
+        y32, y16 = torch.full_like(x32, np.nan), torch.full_like(x32, np.nan)
+        P.spmv_lowp(x32, y32)
+        P16.spmv_lowp(x32, y16)
+        torch.cuda.synchronize()
+        assert P.check() == 0 and P16.check() == 0
+        out[lay] = [t.cpu().numpy() for t in (y, yp, yn, y32, y16)]
+    for a, b in zip(out[0], out[2]):
+        assert np.array_equal(a, b)
+    _check_fp(A, x, out[2][0])
+
+
+def test_halo_layout_cg_matches_sliced(eh):
+    # the CG's fused p.q runs in the same kernel epilogue: identical residual histories
+    A = gen.tet_lap3d(N=24)
+    b = torch.from_numpy(oracle.spmv(A, gen.uniform(A.n, 5))).cuda()
+    hist = {}
+    for lay in (0, 2):
+        P = eh.Plan(A, er_layout=lay)
+        x = torch.zeros_like(b)
+        st, info = P.cg(b, x, rtol=1e-10)
+        assert st == 0, info
+        hist[lay] = (P.cg_history(info["iterations"]), x.cpu().numpy())
+    assert np.array_equal(hist[0][0], hist[2][0]) and np.array_equal(hist[0][1], hist[2][1])
+
+
+def test_halo_layout_unsupported_paths(eh):
+    A = gen.tet_lap3d(N=12)
+    P = eh.Plan(A, er_layout=2)
+    with pytest.raises(eh.EhybError):
+        P.spmm(torch.zeros(A.n, 8, dtype=torch.float64, device="cuda"), torch.zeros(A.n, 8, dtype=torch.float64,
+                                                                                     device="cuda"))
+    with pytest.raises(eh.EhybError):
+        eh.Batch([P])
+    import tempfile, os
+    with tempfile.TemporaryDirectory() as d:
+        with pytest.raises(eh.EhybError):
+            P.save(os.path.join(d, "p.ehyb"))
 
 
 @pytest.mark.parametrize("name", ["hex", "tet", "powerlaw", "ragged_int"])

@@ -57,6 +57,21 @@ def test_golden_plan_matches_hand_derivation_exactly(golden):
         for pos, c, v in g["runs"]["er_slice_entries"]:
             scol[pos], sval[pos] = c, v
         assert np.array_equal(ex["er_scol_low"], scol) and np.array_equal(ex["er_sval_low"], sval)
+    # extra rows in the slab slices, x staged at each partition's halo (hand-derived where the golden gives it)
+    ex = _plan(A, part_vec=g["part_vec"], er_layout=2).export()
+    assert ex["er_layout"] == 2 and ef.same_multiset(ef.decode(ex), ef.triplets(A))
+    if "halo" in g:
+        h = g["halo"]
+        want_col = np.zeros(h["slice_pos"][-1], np.uint16)
+        want_val = np.zeros(h["slice_pos"][-1])
+        for pos, c, v in h["ell_entries"]:
+            want_col[pos], want_val[pos] = c, v
+        for k in ("slice_pos", "halo_ptr", "halo_new", "er_slice_pos"):
+            assert list(ex[k]) == h[k], k
+        assert list(ex["new_to_old"]) == g["plan"]["new_to_old"]
+        assert list(ex["row_ell_count"]) == g["plan"]["row_ell_count"]
+        assert list(ex["row_er_count"]) == g["plan"]["row_er_count"]
+        assert np.array_equal(ex["ell_col"], want_col) and np.array_equal(ex["ell_val"], want_val)
 
 
 def _invariants(A, ex, cap=None, width_cap=0):
@@ -89,7 +104,8 @@ def _invariants(A, ex, cap=None, width_cap=0):
             assert np.all(np.diff(er_cnt[rows]) <= 0)                    # ER lines by count, descending
         ns = ex["slice_ptr"][p + 1] - ex["slice_ptr"][p]
         assert ns == -(-(pp[p + 1] - pp[p]) // (32 // ex["tpr"]))         # slices never straddle partitions
-    assert np.all(ex["ell_col"].astype(np.int64) < np.maximum(1, sizes.max(initial=1)))
+    stage = sizes + (np.diff(ex["halo_ptr"]) if ex["er_layout"] == 2 else 0)   # own rows (+ halo, layout 2)
+    assert np.all(ex["ell_col"].astype(np.int64) < np.maximum(1, stage.max(initial=1)))
     if width_cap:
         assert cnt.max(initial=0) <= width_cap
     assert np.array_equal(np.sort(np.unique(ex["er_row"])), np.sort(ex["er_row"]))  # one line per row
@@ -103,7 +119,9 @@ def _invariants(A, ex, cap=None, width_cap=0):
 @pytest.mark.parametrize("kw", [dict(), dict(ell_tpr=2), dict(ell_tpr=4, er_tpr=8), dict(ell_tpr=32),
                                 dict(ell_width_cap=5), dict(slice_rows=37), dict(slice_rows=1),
                                 dict(lowp=1), dict(lowp=2), dict(er_layout=1), dict(er_layout=1, ell_tpr=4),
-                                dict(er_layout=1, ell_width_cap=3, slice_rows=50)])
+                                dict(er_layout=1, ell_width_cap=3, slice_rows=50), dict(er_layout=2),
+                                dict(er_layout=2, ell_tpr=4), dict(er_layout=2, ell_width_cap=3, slice_rows=50),
+                                dict(er_layout=2, lowp=2, slice_rows=1)])
 def test_decode_multiset_random_ragged(kw):
     A = gen.random_csr(700, 7, mean_row=9, empty_frac=0.1, long_rows=3, long_len=400, duplicates=True)
     ex = _plan(A, **kw).export()
@@ -111,7 +129,7 @@ def test_decode_multiset_random_ragged(kw):
     _invariants(A, ex, cap=kw.get("slice_rows"), width_cap=kw.get("ell_width_cap", 0))
 
 
-@pytest.mark.parametrize("er_layout", [0, 1])
+@pytest.mark.parametrize("er_layout", [0, 1, 2])
 @pytest.mark.parametrize("name", ["fem2d", "hex", "tet"])
 def test_decode_multiset_fem(name, er_layout):
     A = {"fem2d": lambda: gen.fem2d_p1(N=40), "hex": lambda: gen.hex_elast3d(N=8),
@@ -191,3 +209,68 @@ def test_plan_for_k_right_hand_sides_follows_eq1(k, kc):
     P = _plan(A, spmm_rhs=k, num_sms=152)
     K, vec = ef.eq1(A.n, 8 * kc, 152, 232448 - 1024 - 32 - 16 * kc)
     assert P.info()["slice_rows"] == vec
+
+
+def _halo_of(A, ex):
+    """Per partition, the sorted distinct plan-numbering columns of its rows' entries outside it, from the CSR
+    matrix and the exported permutation alone."""
+    n2o = np.asarray(ex["new_to_old"], np.int64)
+    o2n = np.empty_like(n2o)
+    o2n[n2o] = np.arange(A.n)
+    pp = np.asarray(ex["part_ptr"], np.int64)
+    out = []
+    for p in range(len(pp) - 1):
+        cols = []
+        for r in range(pp[p], pp[p + 1]):
+            i = n2o[r]
+            c = o2n[A.col[A.row_ptr[i]:A.row_ptr[i + 1]]]
+            cols.append(c[(c < pp[p]) | (c >= pp[p + 1])])
+        out.append(np.unique(np.concatenate(cols)) if cols else np.zeros(0, np.int64))
+    return out
+
+
+@pytest.mark.parametrize("name", ["ragged", "tet", "hex"])
+def test_halo_layout_lists_slots_and_partition(name):
+    A = {"ragged": lambda: gen.random_csr(900, 3, mean_row=9, empty_frac=0.1, long_rows=3, long_len=300,
+                                          duplicates=True),
+         "tet": lambda: gen.tet_lap3d(N=14), "hex": lambda: gen.hex_elast3d(N=9)}[name]()
+    e0 = _plan(A, slice_rows=300).export()
+    P2 = _plan(A, slice_rows=300, er_layout=2)
+    e2 = P2.export()
+    # same partition, permutation and per-row counts as the sliced layout; no sliced extra-row slots
+    for k in ("new_to_old", "part_ptr", "slice_ptr", "row_ell_count", "row_er_count"):
+        assert np.array_equal(e0[k], e2[k]), k
+    assert not np.any(e2["er_slice_pos"]) and e2["er_scol"].size == 0
+    # the halo lists are exactly the out-of-partition columns of each partition, ascending and distinct
+    want = _halo_of(A, e2)
+    hp = np.asarray(e2["halo_ptr"], np.int64)
+    assert hp[0] == 0 and np.all(np.diff(hp) >= 0)
+    for p, h in enumerate(want):
+        assert np.array_equal(e2["halo_new"][hp[p]:hp[p + 1]], h), p
+    # each row's slots: its own entries then its extra ones, both in CSR order (the sliced layout's order)
+    rows, cols, vals = ef.decode(e2)
+    r0, c0, v0 = ef.decode(e0)
+    order2 = {}
+    for r, c, v in zip(rows, cols, vals):
+        order2.setdefault(int(r), []).append((int(c), float(v)))
+    order0 = {}
+    for r, c, v in zip(r0, c0, v0):
+        order0.setdefault(int(r), []).append((int(c), float(v)))
+    assert order2 == order0
+    info = P2.info()
+    stage = max(int(np.diff(e2["part_ptr"])[p]) + len(h) for p, h in enumerate(want))
+    assert info["max_stage_rows"] == stage and info["n_halo"] == hp[-1] and info["er_layout"] == 2
+    assert info["bytes_effective"] == 10 * A.nnz + 12 * int(hp[-1]) + 16 * A.n
+
+
+def test_halo_layout_too_large_is_refused():
+    # 4 partitions of 25,000 rows, every row with entries all over the matrix: each halo holds most of the
+    # other 75,000 rows, past the 16-bit local column
+    import paper_2204_06666_gb300 as eh
+    n = 100000
+    A = gen.random_csr(n, 5, mean_row=20)
+    pv = (np.arange(n) // 25000).astype(np.int32)
+    with pytest.raises(eh.EhybError) as e:
+        _plan(A, part_vec=pv, er_layout=2)
+    assert e.value.status == 4
+    assert _plan(A, part_vec=pv).info()["er_layout"] == 0
