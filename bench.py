@@ -309,7 +309,8 @@ def run_ehyb(args):
     x = gen.uniform(A.n, w["seed_x"])
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    plan = eh.Plan(A, partitioner=args.partitioner, er_layout=args.er_layout)
+    plan = eh.Plan(A, partitioner=args.partitioner, er_layout=args.er_layout, slice_rows=args.slice_rows,
+                   block_threads=args.block_threads)
     plan_ms = (time.perf_counter() - t0) * 1e3
     info = plan.info()
     xd = torch.from_numpy(x).to(dev)
@@ -525,7 +526,7 @@ def run_ehyb(args):
                               f"{FLUSH_BYTES >> 20} MB write that flushes L2 (cold); warm back-to-back steps "
                               f"in 'warm'"),
                        "partitioner": ["greedy growing", "multilevel"][args.partitioner],
-                       "er_layout": info["er_layout"],
+                       "er_layout": info["er_layout"], "block_threads": info["block_threads"],
                        "nparts": info["nparts"], "slice_rows": info["slice_rows"],
                        "er_fraction": info["er_nnz"] / A.nnz, "er_tpr": info["er_tpr"],
                        "block_threads": info["block_threads"]},
@@ -977,6 +978,10 @@ def main():
     ap.add_argument("--skip-csr", action="store_true")
     ap.add_argument("--er-layout", type=int, default=0, choices=[0, 1, 2],
                     help="extra-row layout of the SpMV and --lowp plans (options.er_layout)")
+    ap.add_argument("--slice-rows", type=int, default=0,
+                    help="rows per partition of the SpMV plan (options.slice_rows; 0 = Eq. 1)")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="threads per block of the SpMV plan (options.block_threads; 0 = automatic)")
     ap.add_argument("--partitioner", type=int, default=0, choices=[0, 1],
                     help="PartVec of the SpMV plan: 0 greedy graph growing, 1 multilevel")
     ap.add_argument("--plan-io", action="store_true", help="also time saving the plan to a file and loading it")
