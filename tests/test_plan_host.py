@@ -274,3 +274,20 @@ def test_halo_layout_too_large_is_refused():
         _plan(A, part_vec=pv, er_layout=2)
     assert e.value.status == 4
     assert _plan(A, part_vec=pv).info()["er_layout"] == 0
+
+
+def test_halo_layout_refused_where_it_is_not_supported(tmp_path):
+    # plan files and row shards read the separate extra-row arrays: a halo-layout plan is refused there
+    import paper_2204_06666_gb300 as eh
+    A = gen.tet_lap3d(N=10)
+    P = _plan(A, er_layout=2)
+    with pytest.raises(eh.EhybError) as e:
+        P.save(str(tmp_path / "p.ehyb"))
+    assert e.value.status == 7
+    with pytest.raises(eh.EhybError) as e:
+        eh.Shard(P, 2, 0)
+    assert e.value.status == 7
+    _plan(A).save(str(tmp_path / "q.ehyb"))  # the sliced layout saves
+    with pytest.raises(eh.EhybError) as e:
+        _plan(A, er_layout=3)
+    assert e.value.status == 1
