@@ -391,19 +391,30 @@ def test_csr_baseline_parity(eh, tpr):
     _check_fp(B, xb, yd.cpu().numpy())
 
 
-def test_edge_cases(eh):
+@pytest.mark.parametrize("er_layout", [0, 2])
+def test_edge_cases(eh, er_layout):
     for n in (1, 2, 31, 32, 33, 65):
         A = gen.random_csr(n, n, mean_row=3, int_values=True, empty_frac=0.3)
         x = gen.int_vector(n, n)
-        _, y = _run(eh, A, x, slice_rows=16)
+        _, y = _run(eh, A, x, slice_rows=16, er_layout=er_layout)
         assert np.array_equal(y, oracle.spmv(A, x)), n
     Z = gen.CSR(40, np.zeros(41, np.int64), np.zeros(0, np.int32), np.zeros(0))   # no entries at all
-    _, y = _run(eh, Z, np.ones(40))
+    _, y = _run(eh, Z, np.ones(40), er_layout=er_layout)
     assert np.all(y == 0)
     E = gen.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
-    P = eh.Plan(E)
+    P = eh.Plan(E, er_layout=er_layout)
     P.spmv(torch.zeros(1, dtype=torch.float64, device="cuda")[:0], torch.zeros(1, dtype=torch.float64, device="cuda")[:0])
     assert P.check() == 0
+    # every row's entries outside its one-row partition: the halo holds all of them
+    n = 64
+    rp = np.arange(n + 1, dtype=np.int64) * 3
+    col = np.stack([(np.arange(n) + k) % n for k in (7, 19, 41)], axis=1).ravel().astype(np.int32)
+    D = gen.CSR(n, rp, col, np.arange(1, 3 * n + 1, dtype=np.float64))
+    x = gen.int_vector(n, 3)
+    P, y = _run(eh, D, x, slice_rows=1, er_layout=er_layout)
+    assert np.array_equal(y, oracle.spmv(D, x))
+    if er_layout == 2:
+        assert P.info()["n_halo"] == 3 * n and P.info()["max_stage_rows"] == 4
 
 
 def test_staging_wait_timeout_is_reported_and_context_survives(eh):
