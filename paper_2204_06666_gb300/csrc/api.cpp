@@ -373,6 +373,9 @@ ehyb_status_t plan_finalize(std::unique_ptr<ehyb_plan_s>& P, const ehyb_options_
   D.er_layout = H.er_layout;
   D.max_part_rows = H.max_part_rows;
   D.max_stage_rows = H.max_stage_rows;
+  D.max_part_slices = 0;
+  for (int32_t p = 0; p < H.nparts; ++p)
+    D.max_part_slices = std::max(D.max_part_slices, H.slice_ptr[(size_t)p + 1] - H.slice_ptr[(size_t)p]);
   {  // batch depth: mean slab + sliced-ER slots per lane of a slice (measured: 6 is faster from about 32 up)
     const double w = mean_slice_width(H);
     D.kbatch = (H.er_layout == 0 && w >= 32.0) ? 6 : 8;

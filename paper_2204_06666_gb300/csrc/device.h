@@ -13,8 +13,9 @@ struct DevPlan {
   int32_t nparts = 0, tpr = 1, er_tpr = 1, threads = 512;
   int32_t max_part_rows = 0;
   int32_t max_stage_rows = 0;  // largest rows + halo of a partition: the staged x elements (er_layout 2)
+  int32_t max_part_slices = 0;  // most slices of one partition (entries of the fused kernel's slice table)
   int32_t kbatch = 8;  // FP64 batch depth (two pipelined half-batches): 6 on wide slices (>= 32 slots a lane), else 8;
-                       // the FP32 / BF16 kernels hold 12 (column-major copies) or 16 (copies in 4-slot groups)
+                       // the FP32 / BF16 kernels hold 12 (column-major copies) or 16 / 32 (copies in runs of four)
   const int32_t* new_to_old = nullptr;
   const int32_t* part_ptr = nullptr;
   const int32_t* slice_ptr = nullptr;

@@ -9,10 +9,12 @@
 //        EHYB_ERR_TIMEOUT in the plan status word and returns);
 //     3. each warp takes 32-lane slices of the partition from a shared counter (the dynamic
 //        slice balancing of Alg. 3) and runs y[row] = sum_k ValELL * CachedVec[ColELL] with the
-//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot, six to twelve slots of
+//        16-bit column offsets of Sec. 3.4, exactly one FMA per stored slot, six to 32 slots of
 //        values and columns loaded ahead of their FMAs to keep enough bytes in flight; the FP32 / BF16
-//        copies of plans with wide slices keep each lane's slots in runs of four (slot_pos in
-//        plan.h) and read a run's values and columns with one vector load each;
+//        copies (sliced ER layout) keep each lane's slots in runs of four (slot_pos in plan.h), read a
+//        run's values and columns with one vector load each and hold them packed until their FMAs;
+//        each block keeps its partition's slice table (where each slice starts, its widths) in shared
+//        memory, so claiming the next slice costs no global load;
 //     4. extra-row (ER) entries, three layouts:
 //        - sliced (er_layout 0, default): the ER entries of the slice's own rows are stored in
 //          the same lane -> row arrangement right behind it (the paper stores its ER part as
@@ -219,7 +221,60 @@ __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __r
   return acc;
 }
 
-// ---- slots in runs of four per lane (the FP32 / BF16 copies of plans with wide slices; slot_pos, group 4):
+// ---- narrow low-precision slices in one shot
+constexpr int kShot = 16;   // slab slots a lane of a narrow FP32 / BF16 slice loads at once
+constexpr int kShotEr = 4;  // extra-row slots likewise
+
+// acc = sum of the slice's slab slots (w <= kShot) and then its extra-row slots (we <= kShotEr) for one lane,
+// column-major copies: every value and column of the lane is loaded at once, then the extra-row gathers of x,
+// then the FMAs in slot order (slab, then extra rows: the order of slab_dot followed by er_dot, so the same
+// bits).  A slice then costs one memory round trip for its slots (plus one for the gathers) instead of one
+// per half-batch: a 2- or 4-byte value leaves too few bytes in flight per warp for the pipelined loop.  The
+// guards are uniform across the warp (the widths are the slice's).
+template <typename V, typename X>
+__device__ __forceinline__ X slice_shot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
+                                        const X* xs, int lim, const V* __restrict__ evp,
+                                        const int32_t* __restrict__ ecp, int we, const X* __restrict__ xg,
+                                        int64_t elim, int32_t* status) {
+  X v[kShot];
+  int c[kShot];
+#pragma unroll
+  for (int u = 0; u < kShot; ++u) {
+    v[u] = X(0);
+    c[u] = 0;
+    if (u < w) {
+      v[u] = load_val<V, X>(vp + 32 * u);
+      c[u] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * u)), lim, status);
+    }
+  }
+  X ev[kShotEr];
+  int ec[kShotEr];
+#pragma unroll
+  for (int u = 0; u < kShotEr; ++u) {
+    ev[u] = X(0);
+    ec[u] = 0;
+    if (u < we) {
+      ev[u] = load_val<V, X>(evp + 32 * u);
+      ec[u] = checked(__ldcs(ecp + 32 * u), elim, status);
+    }
+  }
+  X ex[kShotEr];
+#pragma unroll
+  for (int u = 0; u < kShotEr; ++u) {
+    ex[u] = X(0);
+    if (u < we) ex[u] = __ldg(xg + ec[u]);
+  }
+  X acc = X(0);
+#pragma unroll
+  for (int u = 0; u < kShot; ++u)
+    if (u < w) acc = fma_t(v[u], xs[c[u]], acc);
+#pragma unroll
+  for (int u = 0; u < kShotEr; ++u)
+    if (u < we) acc = fma_t(ev[u], ex[u], acc);
+  return acc;
+}
+
+// ---- slots in runs of four per lane (the FP32 / BF16 copies of the sliced ER layout; slot_pos, group 4):
 // a lane reads a run's four values with one 16-byte (FP32) or 8-byte (BF16) load and its four 16-bit columns
 // with one 8-byte load; the w mod 4 slots after the runs are column-major.
 constexpr int kGroup = 4;
@@ -254,61 +309,108 @@ __device__ __forceinline__ void ld_cols(const int32_t* p, int (&c)[4]) {  // fou
   c[3] = v.w;
 }
 
-// slab_dot on runs of four: vb, cb = the slice's first slot; half-batches of KB/8 runs (KB slots in flight),
-// then the column-major tail.  Same slot order, same result as slab_dot on the column-major copy.
+// A run of four slots as loaded: values and 16-bit columns stay packed in registers until their FMAs (a BF16
+// run takes four registers, an FP32 run six), so a lane holds twice the slots in flight for its registers.
+template <typename V>
+struct Run;
+template <>
+struct Run<float> {
+  float4 v;
+  uint2 c;
+};
+template <>
+struct Run<uint16_t> {
+  uint2 v;
+  uint2 c;
+};
+__device__ __forceinline__ void ld_run(const float* vp, const uint16_t* cp, Run<float>& r) {
+  r.v = __ldcs(reinterpret_cast<const float4*>(vp));
+  r.c = __ldcs(reinterpret_cast<const uint2*>(cp));
+}
+__device__ __forceinline__ void ld_run(const uint16_t* vp, const uint16_t* cp, Run<uint16_t>& r) {
+  r.v = __ldcs(reinterpret_cast<const uint2*>(vp));
+  r.c = __ldcs(reinterpret_cast<const uint2*>(cp));
+}
+__device__ __forceinline__ void zero_run(Run<float>& r) {
+  r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+  r.c = make_uint2(0u, 0u);
+}
+__device__ __forceinline__ void zero_run(Run<uint16_t>& r) {
+  r.v = make_uint2(0u, 0u);
+  r.c = make_uint2(0u, 0u);
+}
+__device__ __forceinline__ float run_val(const Run<float>& r, int t) {
+  return t == 0 ? r.v.x : t == 1 ? r.v.y : t == 2 ? r.v.z : r.v.w;
+}
+__device__ __forceinline__ float run_val(const Run<uint16_t>& r, int t) {  // the lower address is the low half
+  const uint32_t h = t < 2 ? r.v.x : r.v.y;
+  return __uint_as_float((t & 1) ? (h & 0xffff0000u) : (h << 16));
+}
+__device__ __forceinline__ int run_col(const uint2& c, int t) {
+  const uint32_t h = t < 2 ? c.x : c.y;
+  return (int)((t & 1) ? (h >> 16) : (h & 0xffffu));
+}
+// acc += the run's four products, in slot order
+template <typename V>
+__device__ __forceinline__ float fma_run(const Run<V>& r, const float* xs, float acc, int lim, int32_t* status) {
+#pragma unroll
+  for (int t = 0; t < kGroup; ++t) acc = fmaf(run_val(r, t), xs[checked(run_col(r.c, t), lim, status)], acc);
+  return acc;
+}
+
+// slab_dot on runs of four: vb, cb = the slice's first slot; half-batches of NG = KB/8 runs (KB slots in
+// flight), the next half-batch's loads issued before the current one's FMAs, the last half-batch guarded by
+// the run count; the w mod 4 column-major slots after the runs are loaded with the first half-batch and
+// multiplied last.  Same slot order, same result as slab_dot on the column-major copy.
 template <typename V, typename X, int KB>
 __device__ __forceinline__ X slab_dot_runs(const V* __restrict__ vb, const uint16_t* __restrict__ cb, int lane, int w,
                                            const X* xs, X acc, int lim, int32_t* status) {
   constexpr int NG = KB / 8;
   static_assert(NG >= 1 && KB % 8 == 0, "runs: half-batches of whole runs");
   const int ng = w >> 2;
+  const int nt = w & (kGroup - 1);
   const V* vp = vb + kGroup * lane;  // run g of this lane: vp + 128 g
   const uint16_t* cp = cb + kGroup * lane;
-  int g = 0;
-  if (ng >= NG) {
-    X va[NG][kGroup];
-    int ca[NG][kGroup];
+  Run<V> ra[NG];
+#pragma unroll
+  for (int u = 0; u < NG; ++u) {
+    zero_run(ra[u]);
+    if (u < ng) ld_run(vp + 128 * (int64_t)u, cp + 128 * (int64_t)u, ra[u]);
+  }
+  // column-major tail: slot 4 ng + t of this lane at the slice's first slot + 128 ng + 32 t + lane
+  X tv[kGroup - 1];
+  int tc[kGroup - 1];
+#pragma unroll
+  for (int t = 0; t < kGroup - 1; ++t) {
+    tv[t] = X(0);
+    tc[t] = 0;
+    if (t < nt) {
+      const int64_t o = 128 * (int64_t)ng + 32 * t + lane;
+      tv[t] = load_val<V, X>(vb + o);
+      tc[t] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cb + o)), lim, status);
+    }
+  }
+  int g = NG;  // runs [g - NG, g) are in ra
+  for (; g < ng; g += NG) {
+    Run<V> rb[NG];
 #pragma unroll
     for (int u = 0; u < NG; ++u) {
-      ld_group(vp + 128 * (int64_t)u, va[u]);
-      ld_cols(cp + 128 * (int64_t)u, ca[u]);
-    }
-    for (g = NG; g + NG <= ng; g += NG) {
-      X vn[NG][kGroup];
-      int cn[NG][kGroup];
-#pragma unroll
-      for (int u = 0; u < NG; ++u) {
-        ld_group(vp + 128 * (int64_t)(g + u), vn[u]);
-        ld_cols(cp + 128 * (int64_t)(g + u), cn[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < NG; ++u)
-#pragma unroll
-        for (int t = 0; t < kGroup; ++t) acc = fma_t(va[u][t], xs[checked(ca[u][t], lim, status)], acc);
-#pragma unroll
-      for (int u = 0; u < NG; ++u)
-#pragma unroll
-        for (int t = 0; t < kGroup; ++t) {
-          va[u][t] = vn[u][t];
-          ca[u][t] = cn[u][t];
-        }
+      zero_run(rb[u]);
+      if (g + u < ng) ld_run(vp + 128 * (int64_t)(g + u), cp + 128 * (int64_t)(g + u), rb[u]);
     }
 #pragma unroll
-    for (int u = 0; u < NG; ++u)
+    for (int u = 0; u < NG; ++u) acc = fma_run(ra[u], xs, acc, lim, status);  // g < ng: all NG runs are stored
 #pragma unroll
-      for (int t = 0; t < kGroup; ++t) acc = fma_t(va[u][t], xs[checked(ca[u][t], lim, status)], acc);
+    for (int u = 0; u < NG; ++u) ra[u] = rb[u];
   }
-  for (; g < ng; ++g) {  // fewer than NG whole runs left
-    X v[kGroup];
-    int c[kGroup];
-    ld_group(vp + 128 * (int64_t)g, v);
-    ld_cols(cp + 128 * (int64_t)g, c);
+  const int last = ng - (g - NG);  // 0..NG stored runs in ra
 #pragma unroll
-    for (int t = 0; t < kGroup; ++t) acc = fma_t(v[t], xs[checked(c[t], lim, status)], acc);
-  }
-  // column-major tail: slot k (k >= 4 ng) of this lane at the slice's first slot + 32 k + lane
-  return slab_dot<V, X, 2>(vb + 128 * (int64_t)ng + lane, cb + 128 * (int64_t)ng + lane, w & (kGroup - 1), xs, acc,
-                           lim, status);
+  for (int u = 0; u < NG; ++u)
+    if (u < last) acc = fma_run(ra[u], xs, acc, lim, status);
+#pragma unroll
+  for (int t = 0; t < kGroup - 1; ++t)
+    if (t < nt) acc = fma_t(tv[t], xs[tc[t]], acc);
+  return acc;
 }
 
 // er_dot on runs of four: batches of kErGroups runs (values and columns loaded, then their x gathers, then
@@ -350,8 +452,31 @@ __device__ __forceinline__ X er_dot_runs(const V* __restrict__ vb, const int32_t
 #pragma unroll
     for (int t = 0; t < kGroup; ++t) acc = fma_t(v[t], xv[t], acc);
   }
-  return er_dot<V, X, 2>(vb + 128 * (int64_t)ng + lane, cb + 128 * (int64_t)ng + lane, w & (kGroup - 1), xg, acc,
-                         lim, status);
+  // the w mod 4 column-major slots: loads, then gathers, then FMAs, guarded (one round trip each)
+  const int nt = w & (kGroup - 1);
+  const V* tvp = vb + 128 * (int64_t)ng + lane;
+  const int32_t* tcp = cb + 128 * (int64_t)ng + lane;
+  X tv[kGroup - 1];
+  int tc[kGroup - 1];
+#pragma unroll
+  for (int t = 0; t < kGroup - 1; ++t) {
+    tv[t] = X(0);
+    tc[t] = 0;
+    if (t < nt) {
+      tv[t] = load_val<V, X>(tvp + 32 * t);
+      tc[t] = checked(__ldcs(tcp + 32 * t), lim, status);
+    }
+  }
+  X tx[kGroup - 1];
+#pragma unroll
+  for (int t = 0; t < kGroup - 1; ++t) {
+    tx[t] = X(0);
+    if (t < nt) tx[t] = __ldg(xg + tc[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < kGroup - 1; ++t)
+    if (t < nt) acc = fma_t(tv[t], tx[t], acc);
+  return acc;
 }
 
 struct KArgs {
@@ -383,6 +508,17 @@ struct KArgs {
   int32_t* dot_arrive;    // optional (with dot_part, one block per partition): arrival counter; the last
   double* dot_result;     //   block reduces the partials into *dot_result and resets the counter
   const int32_t* skip;    // optional: the launch does nothing while *skip != 0 (converged solver)
+  int32_t meta_off;       // byte offset of the partition's slice table in dynamic shared memory (0: none)
+  int32_t meta_cap;       //   ... and its capacity in entries (checked build only)
+};
+
+// One slice of a partition in its processing order, as the block keeps it in shared memory: where its slab
+// and extra-row slots start and how many slots a lane has in each.  Staged once per partition, so a warp
+// that claims its next slice reads it from shared memory instead of two dependent global loads
+// (slice_order, then slice_pos).
+struct SliceMeta {
+  int64_t pos, epos;
+  int32_t w, we, s, pad;
 };
 
 // warp-level fixed-order sum of count values (lane-strided, then an xor tree); every lane gets it
@@ -461,6 +597,13 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
     }
   }
   const int bd = blockDim.x;
+  // the slice table (a.meta_off != 0): thread t < s1 - s0 fills entry t; its slice_order load goes out
+  // before the staging of x, its slice_pos loads after it
+  SliceMeta* tbl = a.meta_off ? reinterpret_cast<SliceMeta*>(reinterpret_cast<unsigned char*>(xs) + a.meta_off)
+                              : nullptr;
+  const int ns = s1 - s0;
+  int tslice = -1;
+  if (tbl && tid < ns) tslice = a.slice_order[s0 + tid];
   if (GATHER) {
     // xs[r - a0] = x[new_to_old[r]]: kStage indices, then kStage values in flight per thread (one round
     // covers a partition of kStage * blockDim rows)
@@ -501,6 +644,23 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
         if (j0 + u * bd < nh) xs[checked(pe - a0 + j0 + u * bd, a.smem_elems, a.status)] = v[u];
     }
   }
+  if (tbl) {
+    for (int t = tid; t < ns; t += bd) {
+      const int sl = t == tid ? tslice : a.slice_order[s0 + t];
+      SliceMeta m;
+      m.pos = a.slice_pos[sl];
+      m.w = (int)((a.slice_pos[sl + 1] - m.pos) >> 5);
+      m.epos = 0;
+      m.we = 0;
+      if (ER_SLICED) {
+        m.epos = a.er_slice_pos[sl];
+        m.we = (int)((a.er_slice_pos[sl + 1] - m.epos) >> 5);
+      }
+      m.s = sl;
+      m.pad = 0;
+      tbl[checked(t, a.meta_cap, a.status)] = m;
+    }
+  }
   if (tid == 0) {
     int ok = 1;
     if (bulk_bytes) {
@@ -524,18 +684,30 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
   // (static round-robin when the fused dot product is requested, so its order is fixed)
   constexpr bool dot = DOT;  // a.dot_part is set
   double dacc = 0.0;
+  // metadata of the slice at position j of the processing order (j < s1): from the table, else from global
+  auto slice_meta = [&](int j, int& sj, int64_t& posj, int& wj, int64_t& eposj, int& wej) {
+    if (tbl) {
+      const SliceMeta m = tbl[checked(j - s0, a.meta_cap, a.status)];
+      sj = m.s;
+      posj = m.pos;
+      wj = m.w;
+      eposj = m.epos;
+      wej = m.we;
+      return;
+    }
+    sj = a.slice_order[j];
+    posj = a.slice_pos[sj];
+    wj = (int)((a.slice_pos[sj + 1] - posj) >> 5);
+    if (ER_SLICED) {
+      eposj = a.er_slice_pos[sj];
+      wej = (int)((a.er_slice_pos[sj + 1] - eposj) >> 5);
+    }
+  };
   int i = s0 + warp;  // position in the partition's processing order
-  int s = i < s1 ? a.slice_order[i] : s1;
+  int s = s1;
   int64_t pos = 0, epos = 0;
   int w = 0, we = 0;
-  if (i < s1) {
-    pos = a.slice_pos[s];
-    w = (int)((a.slice_pos[s + 1] - pos) >> 5);
-    if (ER_SLICED) {
-      epos = a.er_slice_pos[s];
-      we = (int)((a.er_slice_pos[s + 1] - epos) >> 5);
-    }
-  }
+  if (i < s1) slice_meta(i, s, pos, w, epos, we);
   while (i < s1) {
     // reserve the next slice and start its metadata loads before working on this one
     int inxt;
@@ -546,17 +718,10 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       if (lane == 0) t = atomicAdd(&bs.slice_counter, 1);
       inxt = __shfl_sync(FULL, t, 0);
     }
-    const int nxt = inxt < s1 ? a.slice_order[inxt] : s1;
+    int nxt = s1;
     int64_t npos = 0, nepos = 0;
     int nw = 0, nwe = 0;
-    if (inxt < s1) {
-      npos = a.slice_pos[nxt];
-      nw = (int)((a.slice_pos[nxt + 1] - npos) >> 5);
-      if (ER_SLICED) {
-        nepos = a.er_slice_pos[nxt];
-        nwe = (int)((a.er_slice_pos[nxt + 1] - nepos) >> 5);
-      }
-    }
+    if (inxt < s1) slice_meta(inxt, nxt, npos, nw, nepos, nwe);
     X acc;
     if constexpr (RUNS) {  // the copy in runs of four slots (its own column arrays are in a.ell_col / a.er_scol*)
       acc = slab_dot_runs<V, X, KB>(ell_val + pos, a.ell_col + pos, lane, w, xsl, X(0), pe - pb + nh, a.status);
@@ -684,6 +849,8 @@ inline KArgs make_kargs(const DevPlan& P) {
   a.dot_arrive = nullptr;
   a.dot_result = nullptr;
   a.skip = nullptr;
+  a.meta_off = 0;
+  a.meta_cap = 0;
   return a;
 }
 

@@ -60,7 +60,7 @@ double mean_slice_width(const HostPlan& P) {
 
 void make_lowp_copies(HostPlan& P, int lowp, int group, int threads) {
   if (lowp == 0) return;
-  if (group == 0) group = mean_slice_width(P) >= 32.0 ? kSlotGroup : 1;
+  if (group == 0) group = kSlotGroup;  // runs measured faster than column-major copies on every workload
   if (P.er_layout != 0) group = 1;  // the run loops read the sliced extra-row layout only
   P.lowp_group = group;
   const int T = planner_threads(threads);

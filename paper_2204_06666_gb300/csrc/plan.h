@@ -57,7 +57,7 @@ struct PlanParams {
   int32_t ell_width_cap = 0;  // 0 = unlimited
   int32_t ell_tpr = 1;        // lanes per row in a slab slice
   int32_t lowp = 0;           // 0 none, 1 fp32, 2 bf16 value copies
-  int32_t lowp_group = 0;     // slot layout of the value copies: 1, 4, or 0 = 4 on wide slices (make_lowp_copies)
+  int32_t lowp_group = 0;     // slot layout of the value copies: 1, 4, or 0 = 4 (make_lowp_copies)
   int32_t er_layout = 0;      // 0: ER entries sliced with the slab slices; 1: ER lines in CSR; 2: in the slab
                               //    slices after each row's own entries, x staged at the partition's halo
   const int32_t* part_vec = nullptr;

@@ -277,8 +277,11 @@ ehyb_status_t ehyb_shard_create(ehyb_plan_t plan, int32_t nranks, int32_t rank, 
   D.kbatch = PD.kbatch;
   D.wait_timeout_ns = PD.wait_timeout_ns;
   D.max_part_rows = 0;
-  for (int32_t p = 0; p < D.nparts; ++p)
+  D.max_part_slices = 0;
+  for (int32_t p = 0; p < D.nparts; ++p) {
     D.max_part_rows = std::max(D.max_part_rows, S->part_ptr[(size_t)p + 1] - S->part_ptr[(size_t)p]);
+    D.max_part_slices = std::max(D.max_part_slices, S->slice_ptr[(size_t)p + 1] - S->slice_ptr[(size_t)p]);
+  }
   if (!S->host_only) {
     cudaStream_t s = (cudaStream_t)stream;
     CKS(cudaGetDevice(&S->device));

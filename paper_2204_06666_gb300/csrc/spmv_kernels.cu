@@ -14,10 +14,15 @@ namespace {
 using namespace core;
 
 // batch depth of the FP32 / BF16 kernels: a 4- or 2-byte value needs more slots in flight than an FP64 one
-// (12 measured best among 8, 12, 16 and 24: tet 126^3 FP32 50.0 -> 49.0 us, BF16 52.0 -> 48.2 us); 16 (four
-// runs of four) on copies laid out in runs
+// (12 measured best among 8, 12, 16 and 24: tet 126^3 FP32 50.0 -> 49.0 us, BF16 52.0 -> 48.2 us).  On copies
+// laid out in runs of four, whose registers hold the runs packed: 16 slots for FP32 (an FP32 run takes six
+// registers; 32 spill), 32 for BF16 (four registers a run; tet 126^3 42.7 -> 41.4 us, hex 48^3 29.0 -> 26.8),
+// except in the kernels with the fused dot product, where 32 spill.
 constexpr int kLowBatch = 12;
-constexpr int kRunBatch = 16;
+template <typename V, bool DOT>
+constexpr int run_batch() {
+  return (sizeof(V) == 2 && !DOT) ? 32 : 16;
+}
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT, bool GATHER = false,
           int KB = (sizeof(V) == 8 ? kBatch : kLowBatch), bool RUNS = false>
 __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restrict__ ell_val,
@@ -99,11 +104,12 @@ static cudaError_t set_smem(int bytes) {
     if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, false, kWideBatch>, attr, bytes))) return e;
   }
   if constexpr (!std::is_same<V, double>::value) {  // the copies laid out in runs of four (sliced ER layout)
-    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, false, kRunBatch, true>, attr, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false, false, kRunBatch, true>, attr, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true, kRunBatch, true>, attr, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, true, true, kRunBatch, true>, attr, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true, false, kRunBatch, true>, attr, bytes))) return e;
+    constexpr int R = run_batch<V, false>(), RD = run_batch<V, true>();
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, false, R, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, false, false, R, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false, true, R, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, true, true, RD, true>, attr, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true, false, RD, true>, attr, bytes))) return e;
   }
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, true, false>, attr, bytes))) return e;
   if ((e = cudaFuncSetAttribute(ehyb_kernel<V, X, true, false, false>, attr, bytes))) return e;
@@ -114,8 +120,12 @@ static cudaError_t set_smem(int bytes) {
   return cudaFuncSetAttribute(ehyb_kernel<V, X, false, true, true>, attr, bytes);
 }
 
+// dynamic shared memory a fused-kernel launch may use (the attribute kernels_init sets)
+static size_t g_smem_max = 0;
+
 cudaError_t kernels_init(int smem_optin) {
   cudaError_t e;
+  g_smem_max = (size_t)smem_optin;
   if ((e = set_smem<double, double>(smem_optin))) return e;
   if ((e = set_smem<float, float>(smem_optin))) return e;
   return set_smem<uint16_t, float>(smem_optin);
@@ -165,7 +175,8 @@ static void launch_pdl(const DevPlan& P, size_t smem, cudaStream_t s, const KArg
       ar.ell_col = P.ell_col_low;
       ar.er_scol = P.er_scol_low;
       ar.er_scol_old = P.er_scol_old_low;
-      cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, kRunBatch, true>, ar, ev, erv, xp, y);
+      cudaLaunchKernelEx(&cfg, ehyb_kernel<V, X, SCATTER, ER_SLICED, DOT, GATHER, run_batch<V, DOT>(), true>, ar, ev, erv,
+                         xp, y);
       return;
     }
   }
@@ -177,6 +188,13 @@ static void launch_typed(const DevPlan& P, const V* ev, const V* erv_csr, const 
                          int scatter, size_t smem, cudaStream_t s, const DotOut* dot, const int32_t* skip) {
   KArgs a = make_kargs(P);
   a.smem_elems = (int64_t)(smem / sizeof(X));
+  // the partition's slice table after the staged x, when both fit the block's shared memory
+  const size_t tbytes = (size_t)P.max_part_slices * sizeof(SliceMeta);
+  if (P.max_part_slices > 0 && smem + tbytes <= g_smem_max) {
+    a.meta_off = (int32_t)smem;
+    a.meta_cap = P.max_part_slices;
+    smem += tbytes;
+  }
   if (dot) {
     a.dot_part = dot->part;
     a.dot_arrive = dot->arrive;
