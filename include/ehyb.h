@@ -111,7 +111,7 @@ typedef struct {
                                 partitions only */
   int32_t lowp_group;        /* slot layout of the lowp value copies: 1 = column-major like the FP64 arrays,
                                 4 = each lane's slots in runs of four (one vector load per run; the copies get
-                                their own column arrays in that layout), 0 = 4 (1 when er_layout is not 0).
+                                their own column arrays in that layout), 0 = 4 (1 when er_layout is 1).
                                 Results do not depend on it. */
   int32_t spmm_rhs;          /* right-hand sides the plan is built for (ehyb_spmm): when slice_rows is 0 and this is
                                 above 1, Eq. 1 sizes the partitions for a KC-column slice of X per block (KC the

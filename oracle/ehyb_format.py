@@ -48,8 +48,8 @@ GROUP = 4   # slots of one lane kept together in the runs layout of the low-prec
 def slot_index(base: int, width: int, k: int, lane: int, group: int = 1) -> int:
     """Storage index of slot k (0 <= k < width) of lane `lane` in a 32-lane slice of `width` slots per lane that
     starts at `base`.  Alg. 2 stores slot k of every lane side by side (column-major: base + 32 k + lane); that
-    is group 1, the layout of the FP64 arrays.  In group 4 (the library's FP32 / BF16 copies of plans with wide
-    slices) only the last width mod 4 slots keep that order; before them, each lane's slots come in runs of 4
+    is group 1, the layout of the FP64 arrays.  In group 4 (the library's FP32 / BF16 copies in runs of four)
+    only the last width mod 4 slots keep that order; before them, each lane's slots come in runs of 4
     consecutive slots (one vector load), the 32 lanes' runs for slots 4q..4q+3 side by side:
     base + 128 q + 4 lane + (k - 4 q).  Either way [base, base + 32 width) is filled exactly once."""
     grouped = width - width % GROUP if group == GROUP else 0

@@ -61,7 +61,7 @@ double mean_slice_width(const HostPlan& P) {
 void make_lowp_copies(HostPlan& P, int lowp, int group, int threads) {
   if (lowp == 0) return;
   if (group == 0) group = kSlotGroup;  // runs measured faster than column-major copies on every workload
-  if (P.er_layout != 0) group = 1;  // the run loops read the sliced extra-row layout only
+  if (P.er_layout == 1) group = 1;  // the run loops read the sliced extra-row slots (none in the halo layout)
   P.lowp_group = group;
   const int T = planner_threads(threads);
   const size_t stored = P.ell_val.size(), er_nnz = P.er_val.size(), er_stored = P.er_sval.size();

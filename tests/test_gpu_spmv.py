@@ -352,12 +352,12 @@ def test_lowp_runs_layout_bit_identical_to_column_major(eh, lowp, make):
 
 
 def test_lowp_group_auto(eh):
-    # the sliced extra-row layout gets the copies in runs of four, wide (elasticity) and narrow (tet) slices
-    # alike; the other extra-row layouts keep column-major copies
+    # the sliced and halo extra-row layouts get the copies in runs of four, wide (elasticity) and narrow (tet)
+    # slices alike; the CSR-line layout keeps column-major copies
     assert eh.Plan(gen.hex_elast3d(N=14), lowp=2).info()["lowp_group"] == 4
     assert eh.Plan(gen.tet_lap3d(N=20), lowp=2).info()["lowp_group"] == 4
     assert eh.Plan(gen.hex_elast3d(N=14), lowp=2, er_layout=1).info()["lowp_group"] == 1
-    assert eh.Plan(gen.tet_lap3d(N=20), lowp=1, er_layout=2).info()["lowp_group"] == 1
+    assert eh.Plan(gen.tet_lap3d(N=20), lowp=1, er_layout=2).info()["lowp_group"] == 4
     with pytest.raises(eh.EhybError) as e:
         eh.Plan(gen.tet_lap3d(N=8), lowp=1, lowp_group=2)
     assert e.value.status == 1

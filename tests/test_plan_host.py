@@ -291,3 +291,19 @@ def test_halo_layout_refused_where_it_is_not_supported(tmp_path):
     with pytest.raises(eh.EhybError) as e:
         _plan(A, er_layout=3)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("lowp", [1, 2])
+@pytest.mark.parametrize("er_layout", [0, 2])
+def test_lowp_runs_copy_decodes_exactly(lowp, er_layout):
+    # the automatic low-precision layout (runs of four) of the sliced and the halo layouts: with integer values
+    # in [-8, 8] (exact in BF16) the copy decodes to the input entry for entry
+    A = gen.random_csr(900, 5, mean_row=11, int_values=True, empty_frac=0.05, long_rows=2, long_len=300)
+    ex = _plan(A, lowp=lowp, er_layout=er_layout, slice_rows=120).export()
+    assert ex["lowp_group"] == 4
+    assert ef.same_multiset(ef.decode(ef.low_values(ex), group=4), ef.triplets(A))
+    try:  # read in the wrong layout: another multiset, or a structure the decoder rejects
+        wrong = ef.same_multiset(ef.decode(ef.low_values(ex), group=1), ef.triplets(A))
+    except AssertionError:
+        wrong = False
+    assert not wrong
