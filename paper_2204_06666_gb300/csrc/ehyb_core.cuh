@@ -562,8 +562,10 @@ struct BlockState {
 // staged by one bulk asynchronous copy.
 // Returns false (uniformly across the block) when the staging wait ran
 // out of time.
+// TABLE: the launch may provide the partition's slice table (a.meta_off); without it only the global path is
+// compiled (the persistent batch kernel, whose blocks run many partitions one after the other).
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false, bool GATHER = false,
-          int KB = kBatch, bool RUNS = false>
+          int KB = kBatch, bool RUNS = false, bool TABLE = false>
 __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
                                                const V* __restrict__ er_val, const X* __restrict__ xp,
                                                X* __restrict__ y, const int p, X* xs, BlockState& bs) {
@@ -599,8 +601,9 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
   const int bd = blockDim.x;
   // the slice table (a.meta_off != 0): thread t < s1 - s0 fills entry t; its slice_order load goes out
   // before the staging of x, its slice_pos loads after it
-  SliceMeta* tbl = a.meta_off ? reinterpret_cast<SliceMeta*>(reinterpret_cast<unsigned char*>(xs) + a.meta_off)
-                              : nullptr;
+  SliceMeta* tbl = (TABLE && a.meta_off)
+                        ? reinterpret_cast<SliceMeta*>(reinterpret_cast<unsigned char*>(xs) + a.meta_off)
+                        : nullptr;
   const int ns = s1 - s0;
   int tslice = -1;
   if (tbl && tid < ns) tslice = a.slice_order[s0 + tid];

@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
     bs.bar_ready = 0;
     bs.phase = 0;
   }
-  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB, RUNS>(a, ell_val, er_val, xp, y, blockIdx.x,
-                                                            reinterpret_cast<X*>(smem_raw), bs);
+  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB, RUNS, true>(a, ell_val, er_val, xp, y, blockIdx.x,
+                                                                  reinterpret_cast<X*>(smem_raw), bs);
 }
 
 template <typename X>
