@@ -221,59 +221,6 @@ __device__ __forceinline__ X er_dot(const V* __restrict__ vp, const int32_t* __r
   return acc;
 }
 
-// ---- narrow low-precision slices in one shot
-constexpr int kShot = 16;   // slab slots a lane of a narrow FP32 / BF16 slice loads at once
-constexpr int kShotEr = 4;  // extra-row slots likewise
-
-// acc = sum of the slice's slab slots (w <= kShot) and then its extra-row slots (we <= kShotEr) for one lane,
-// column-major copies: every value and column of the lane is loaded at once, then the extra-row gathers of x,
-// then the FMAs in slot order (slab, then extra rows: the order of slab_dot followed by er_dot, so the same
-// bits).  A slice then costs one memory round trip for its slots (plus one for the gathers) instead of one
-// per half-batch: a 2- or 4-byte value leaves too few bytes in flight per warp for the pipelined loop.  The
-// guards are uniform across the warp (the widths are the slice's).
-template <typename V, typename X>
-__device__ __forceinline__ X slice_shot(const V* __restrict__ vp, const uint16_t* __restrict__ cp, int w,
-                                        const X* xs, int lim, const V* __restrict__ evp,
-                                        const int32_t* __restrict__ ecp, int we, const X* __restrict__ xg,
-                                        int64_t elim, int32_t* status) {
-  X v[kShot];
-  int c[kShot];
-#pragma unroll
-  for (int u = 0; u < kShot; ++u) {
-    v[u] = X(0);
-    c[u] = 0;
-    if (u < w) {
-      v[u] = load_val<V, X>(vp + 32 * u);
-      c[u] = checked((int)__ldcs(reinterpret_cast<const unsigned short*>(cp + 32 * u)), lim, status);
-    }
-  }
-  X ev[kShotEr];
-  int ec[kShotEr];
-#pragma unroll
-  for (int u = 0; u < kShotEr; ++u) {
-    ev[u] = X(0);
-    ec[u] = 0;
-    if (u < we) {
-      ev[u] = load_val<V, X>(evp + 32 * u);
-      ec[u] = checked(__ldcs(ecp + 32 * u), elim, status);
-    }
-  }
-  X ex[kShotEr];
-#pragma unroll
-  for (int u = 0; u < kShotEr; ++u) {
-    ex[u] = X(0);
-    if (u < we) ex[u] = __ldg(xg + ec[u]);
-  }
-  X acc = X(0);
-#pragma unroll
-  for (int u = 0; u < kShot; ++u)
-    if (u < w) acc = fma_t(v[u], xs[c[u]], acc);
-#pragma unroll
-  for (int u = 0; u < kShotEr; ++u)
-    if (u < we) acc = fma_t(ev[u], ex[u], acc);
-  return acc;
-}
-
 // ---- slots in runs of four per lane (the FP32 / BF16 copies of the sliced ER layout; slot_pos, group 4):
 // a lane reads a run's four values with one 16-byte (FP32) or 8-byte (BF16) load and its four 16-bit columns
 // with one 8-byte load; the w mod 4 slots after the runs are column-major.
@@ -293,13 +240,6 @@ __device__ __forceinline__ void ld_group(const uint16_t* p, float (&o)[4]) {  //
   o[1] = __uint_as_float(v.x & 0xffff0000u);
   o[2] = __uint_as_float(v.y << 16);
   o[3] = __uint_as_float(v.y & 0xffff0000u);
-}
-__device__ __forceinline__ void ld_cols(const uint16_t* p, int (&c)[4]) {  // four 16-bit columns
-  const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
-  c[0] = (int)(v.x & 0xffffu);
-  c[1] = (int)(v.x >> 16);
-  c[2] = (int)(v.y & 0xffffu);
-  c[3] = (int)(v.y >> 16);
 }
 __device__ __forceinline__ void ld_cols(const int32_t* p, int (&c)[4]) {  // four 32-bit columns
   const int4 v = __ldcs(reinterpret_cast<const int4*>(p));
