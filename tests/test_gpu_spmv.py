@@ -65,6 +65,20 @@ def test_integer_bit_exact_ragged(eh, opt, seed):
     assert np.array_equal(y, oracle.spmv(A, x))
 
 
+@pytest.mark.parametrize("slice_rows", [28922, 4000])
+def test_integer_bit_exact_with_and_without_slice_table(eh, slice_rows):
+    # 28,922 rows (the largest partition the tuner offers): the FP64 slice of x takes 231,392 of the block's
+    # 231,424 bytes of shared memory, so the launch has no room for the partition's slice table (904 slices
+    # x 32 B) and reads each slice's position from global memory; with 4,000 rows the table is staged.  Both
+    # must give the oracle's sums exactly.
+    A = gen.random_csr(61000, 9, mean_row=10, int_values=True, empty_frac=0.05, long_rows=3, long_len=700,
+                       duplicates=True)
+    x = gen.int_vector(A.n, 109)
+    P, y = _run(eh, A, x, slice_rows=slice_rows)
+    assert P.info()["slice_rows"] == slice_rows
+    assert np.array_equal(y, oracle.spmv(A, x))
+
+
 @pytest.mark.parametrize("er_layout", [0, 1, 2])
 @pytest.mark.parametrize("name,N,slice_rows", [("fem2d", 200, 0), ("hex", 16, 0), ("hex", 16, 700),
                                                ("tet", 20, 0), ("tet", 20, 1000)])
