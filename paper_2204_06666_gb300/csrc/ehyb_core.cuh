@@ -504,8 +504,11 @@ struct BlockState {
 // out of time.
 // TABLE: the launch may provide the partition's slice table (a.meta_off); without it only the global path is
 // compiled (the persistent batch kernel, whose blocks run many partitions one after the other).
+// PDL: the kernel was launched with programmatic stream serialization and has not yet waited for the previous
+// grid: the slice table, which reads plan arrays only, is filled first, then griddepcontrol.wait, then every
+// read of x (and of the solver's skip flag) and every write of y.
 template <typename V, typename X, bool SCATTER, bool ER_SLICED, bool DOT = false, bool GATHER = false,
-          int KB = kBatch, bool RUNS = false, bool TABLE = false>
+          int KB = kBatch, bool RUNS = false, bool TABLE = false, bool PDL = false>
 __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restrict__ ell_val,
                                                const V* __restrict__ er_val, const X* __restrict__ xp,
                                                X* __restrict__ y, const int p, X* xs, BlockState& bs) {
@@ -518,6 +521,35 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
   const int pe = a.part_ptr[p + 1];
   const int s0 = a.slice_ptr[p];
   const int s1 = a.slice_ptr[p + 1];
+
+  const int bd = blockDim.x;
+  // ---- 0. the partition's slice table (a.meta_off != 0): entry t = the slice at position s0 + t of the
+  // processing order, its slab / ER start and widths (plan arrays only: before the wait on the previous grid)
+  SliceMeta* tbl = (TABLE && a.meta_off)
+                       ? reinterpret_cast<SliceMeta*>(reinterpret_cast<unsigned char*>(xs) + a.meta_off)
+                       : nullptr;
+  const int ns = s1 - s0;
+  if (tbl) {
+    for (int t = tid; t < ns; t += bd) {
+      const int sl = a.slice_order[s0 + t];
+      SliceMeta m;
+      m.pos = a.slice_pos[sl];
+      m.w = (int)((a.slice_pos[sl + 1] - m.pos) >> 5);
+      m.epos = 0;
+      m.we = 0;
+      if (ER_SLICED) {
+        m.epos = a.er_slice_pos[sl];
+        m.we = (int)((a.er_slice_pos[sl + 1] - m.epos) >> 5);
+      }
+      m.s = sl;
+      m.pad = 0;
+      tbl[checked(t, a.meta_cap, a.status)] = m;
+    }
+  }
+  if (PDL) {
+    pdl_wait();
+    if (a.skip && *a.skip) return true;  // uniform across the grid (a converged solver's flag)
+  }
 
   // ---- 1. stage x_p[pb, pe) into shared memory
   const int a0 = pb & ~(EPV - 1);  // 16-byte aligned start
@@ -538,15 +570,6 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
       if (!a.inject) bulk_g2s(xs, xp + a0, bulk_bytes, &bs.bar);
     }
   }
-  const int bd = blockDim.x;
-  // the slice table (a.meta_off != 0): thread t < s1 - s0 fills entry t; its slice_order load goes out
-  // before the staging of x, its slice_pos loads after it
-  SliceMeta* tbl = (TABLE && a.meta_off)
-                        ? reinterpret_cast<SliceMeta*>(reinterpret_cast<unsigned char*>(xs) + a.meta_off)
-                        : nullptr;
-  const int ns = s1 - s0;
-  int tslice = -1;
-  if (tbl && tid < ns) tslice = a.slice_order[s0 + tid];
   if (GATHER) {
     // xs[r - a0] = x[new_to_old[r]]: kStage indices, then kStage values in flight per thread (one round
     // covers a partition of kStage * blockDim rows)
@@ -585,23 +608,6 @@ __device__ __forceinline__ bool partition_spmv(const KArgs& a, const V* __restri
 #pragma unroll
       for (int u = 0; u < kStage; ++u)
         if (j0 + u * bd < nh) xs[checked(pe - a0 + j0 + u * bd, a.smem_elems, a.status)] = v[u];
-    }
-  }
-  if (tbl) {
-    for (int t = tid; t < ns; t += bd) {
-      const int sl = t == tid ? tslice : a.slice_order[s0 + t];
-      SliceMeta m;
-      m.pos = a.slice_pos[sl];
-      m.w = (int)((a.slice_pos[sl + 1] - m.pos) >> 5);
-      m.epos = 0;
-      m.we = 0;
-      if (ER_SLICED) {
-        m.epos = a.er_slice_pos[sl];
-        m.we = (int)((a.er_slice_pos[sl + 1] - m.epos) >> 5);
-      }
-      m.s = sl;
-      m.pad = 0;
-      tbl[checked(t, a.meta_cap, a.status)] = m;
     }
   }
   if (tid == 0) {

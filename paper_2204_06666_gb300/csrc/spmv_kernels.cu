@@ -32,18 +32,17 @@ __global__ void __launch_bounds__(1024, 1) ehyb_kernel(KArgs a, const V* __restr
   __shared__ BlockState bs;
   // Launched with programmatic stream serialization: the next kernel in the stream may be scheduled at
   // once, so its blocks become resident as this grid's blocks leave and its launch latency overlaps
-  // this grid's tail.  Nothing is read or written before pdl_wait(), which returns when the previous
-  // kernel in the stream has completed and its writes are visible.  (An L2 bulk prefetch of each
-  // warp's first slice before the wait measured slower on the hex workload and is not done.)
+  // this grid's tail.  Before its griddepcontrol.wait (inside partition_spmv) a block reads plan arrays
+  // only (its slice table); the wait returns when the previous kernel in the stream has completed and
+  // its writes are visible, and x, y and the skip flag are touched only after it.  (An L2 bulk prefetch
+  // of each warp's first slice before the wait measured slower on the hex workload and is not done.)
   pdl_launch_dependents();
-  pdl_wait();
-  if (a.skip && *a.skip) return;
   if (threadIdx.x == 0) {
     bs.bar_ready = 0;
     bs.phase = 0;
   }
-  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB, RUNS, true>(a, ell_val, er_val, xp, y, blockIdx.x,
-                                                                  reinterpret_cast<X*>(smem_raw), bs);
+  partition_spmv<V, X, SCATTER, ER_SLICED, DOT, GATHER, KB, RUNS, true, true>(
+      a, ell_val, er_val, xp, y, blockIdx.x, reinterpret_cast<X*>(smem_raw), bs);
 }
 
 template <typename X>

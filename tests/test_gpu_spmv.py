@@ -119,6 +119,28 @@ def test_tet126_full_size(eh):
     assert np.array_equal(y2, y)
 
 
+@pytest.mark.parametrize("name", ["tet126", "hex70"])
+def test_lowp_full_size_as_benchmarked(eh, name):
+    # the FP32 / BF16 products of the mixed-precision solvers on the benchmarked workloads, in the automatic
+    # layout (runs of four held packed) and launch configuration that bench.py --lowp times: every row within
+    # the FP32 rounding bound of the oracle's product with the same rounded values and x
+    A = gen.tet_lap3d() if name == "tet126" else gen.hex_elast3d()
+    x = gen.uniform(A.n, 29)
+    k = np.diff(A.row_ptr).astype(np.float64)
+    bound = 2 * oracle.gamma(k + 6, 2.0 ** -24) * oracle.abs_spmv(A, x)
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    for lowp in (1, 2):
+        P = eh.Plan(A, lowp=lowp)
+        assert P.info()["lowp_group"] == 4
+        yd = torch.full_like(xd, np.nan)
+        P.spmv_lowp(xd, yd)
+        torch.cuda.synchronize()
+        assert P.check() == 0
+        y = yd.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(y - oracle.spmv_low(A, x, bf16=(lowp == 2))) <= bound), lowp
+        del P
+
+
 @pytest.mark.parametrize("make", [lambda: gen.tet_lap3d(N=30), lambda: gen.hex_elast3d(N=16),
                                   lambda: gen.fem2d_p1(N=150),
                                   lambda: gen.random_csr(5000, 3, mean_row=12, empty_frac=0.05, long_rows=4,
