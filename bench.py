@@ -14,6 +14,9 @@ with the warm time in `warm`.  Also reported:
     ncu record while the kernel sources and the plan's layout match it); the FP64 roof is the FMA
     rate ehyb_fp64_fma_peak measures on the device after the timed region;
   * long_window: when fewer than 200 steps are requested, the same product over 2000 more steps;
+  * plan_numbering: the same product with x and y kept in the plan's numbering (ehyb_spmv_permuted, the
+    form a solver iterates in; the permutations happen once, outside the window), back to back, and
+    whether its result permuted back equals the fused entry's bit for bit;
   * the plain vector-CSR kernel on the same GPU (original and EHYB-reordered row order, best
     lanes-per-row of 1..32);
   * preprocessing (plan build) time as a multiple of one SpMV;
@@ -377,6 +380,31 @@ def run_ehyb(args):
         lw_ms = e0.elapsed_time(e1) / LONG_WINDOW_STEPS
         long_window = {"steps": LONG_WINDOW_STEPS, "ms_per_step": lw_ms,
                        "value": flops_per_step / (lw_ms / 1e3) / 1e9, "clocks": clk_long.summary()}
+    # the same product in the plan numbering (ehyb_spmv_permuted: x and y permuted once, outside the window, as
+    # a solver keeps its vectors): back to back beside the line's caller's-numbering figure, and its result,
+    # permuted back, compared bit for bit with the fused entry's
+    plan_numbering = None
+    if not l2_resident:
+        xp, yp, yb = torch.empty_like(xd), torch.empty_like(xd), torch.empty_like(xd)
+        plan.permute(True, xd, xp)
+        for _ in range(max(3, args.warmup)):
+            plan.spmv_permuted(xp, yp)
+        pn_steps = args.steps if args.steps >= 200 else LONG_WINDOW_STEPS
+        torch.cuda.synchronize()
+        _busy(stream)
+        e0.record(stream)
+        for _ in range(pn_steps):
+            plan.spmv_permuted(xp, yp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pn_ms = e0.elapsed_time(e1) / pn_steps
+        plan.permute(False, yp, yb)
+        torch.cuda.synchronize()
+        pn_gbs = float(info["bytes_effective"]) / (pn_ms / 1e3) / 1e9
+        plan_numbering = {"api": "ehyb_spmv_permuted", "steps": pn_steps, "ms_per_step": pn_ms,
+                          "value": flops_per_step / (pn_ms / 1e3) / 1e9, "unit": "GFLOP/s", "effective_gbs": pn_gbs,
+                          "nominal_8tbs_frac": pn_gbs / 8000.0,
+                          "bit_identical_after_permutation": bool(torch.equal(yb, yd))}
     # the FP64 FMA pipe's rate on this device, measured now (the FP64 kernels' ALU roof)
     fp64_peak, fp64_probe_ms = eh.fp64_fma_peak(iters=2048, reps=5)
     # the fused kernel timed alone: events around every launch (they keep consecutive launches from
@@ -538,6 +566,9 @@ def run_ehyb(args):
             "e2e": e2e, "gpu_launches": (1 if fused else 2) * args.steps, "clocks": clocks}
     if warm:
         line["warm"] = warm
+    if plan_numbering:
+        plan_numbering["hbm_frac"] = plan_numbering["effective_gbs"] / measured_peaks()[0]
+        line["plan_numbering"] = plan_numbering
     if long_window:
         line["long_window"] = long_window
     if rank == 0 and not args.no_cpu_baseline:
