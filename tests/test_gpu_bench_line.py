@@ -1,6 +1,7 @@
 """The benchmark's JSON line on a GPU: every key of the contract is present with the right type, the roofline
 block names its bound and a fraction in range, the end-to-end block counts its copies, and the cold timing of
-an L2-resident workload keeps the warm time beside it."""
+an L2-resident workload keeps the warm time beside it; a workload larger than L2 also reports the product in the
+plan's numbering, bit-identical to the fused entry after the permutation."""
 import json
 import os
 import subprocess
@@ -44,6 +45,9 @@ def test_default_workload_line_keeps_the_contract():
     assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0 and c["multicore"]["cores"] >= 1
     assert c["parity"]["rel_l2"] <= c["parity"]["tolerance"]
     assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+    pn = d["plan_numbering"]                # the same product with the vectors kept in the plan's numbering
+    assert pn["api"] == "ehyb_spmv_permuted" and pn["steps"] == 2000 and pn["bit_identical_after_permutation"]
+    assert 0.5 < pn["ms_per_step"] / d["ms_per_step"] < 1.5 and 0 < pn["hbm_frac"] < 1.2
 
 
 def test_l2_resident_workload_is_timed_cold():
@@ -51,6 +55,7 @@ def test_l2_resident_workload_is_timed_cold():
     assert "flushes L2" in d["config"]["l2"]
     assert d["warm"]["ms_per_step"] > 0 and d["warm"]["value"] > 0
     assert d["ms_per_step"] >= 0.8 * d["warm"]["ms_per_step"]     # a flushed step is not faster than a warm one
+    assert "plan_numbering" not in d                                # timed only where inputs exceed L2
 
 
 def test_fp64_probe_measures_a_plausible_rate():
